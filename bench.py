@@ -1,0 +1,340 @@
+"""Benchmark: bucket oblivious sort (bucket ORP + stable LSD radix sort) of n = 2^30 16-byte
+records {uint64 key uniform, uint64 payload = index}, Z = 1024 (B = 2^21), on GB300.
+
+One step = one bos_sort call over the whole array (all butterfly passes, the in-bin permutation,
+the radix histogram and every radix pass), inputs resident in HBM. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--n-log2 30]
+
+--impl reference times the oracle (plain C++, single thread) on a bounded sample of the same
+workload on the host cores. Under torchrun (N > 1) every rank sorts its own independent array
+(replicas: the method has no exchange step on one array), rank 0 prints the line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+Z_DEFAULT = 1024
+REC = 16
+METRIC = "records/sec & HBM GB/s (% roofline), oblivious sort n=2^30 16-B records vs plain"
+UNIT = "records/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n-log2", type=int, default=30)
+    ap.add_argument("--Z", type=int, default=Z_DEFAULT)
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-form and bitonic comparators")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=22)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2008_01765_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t.get(workload, {}).get(kernel)
+        if e and e.get("source_hash") == source_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(n_log2, Z, dist):
+    """The oracle (literal Algorithm 3.1 + in-bin permutation + std::stable_sort), one thread,
+    on a bounded sample of the workload."""
+    import oracle
+    from paper_2008_01765_gb300 import inputs
+    n = 1 << n_log2
+    recs = inputs.make_records(n, REC, dist, seed=1)
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.sort(recs, Z, 1, method=oracle.LITERAL)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"n=2^{n_log2} 16-B records ({dist} u64 keys), Z={Z}, literal Algorithm 3.1 + "
+                      f"in-bin permutation + std::stable_sort, one host thread, {dt:.2f} s"}
+
+
+def run_reference(args):
+    world, rank, _, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    from paper_2008_01765_gb300 import inputs
+    n = 1 << args.cpu_sample_log2
+    recs = inputs.make_records(n, REC, args.dist, seed=1)
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.sort(recs, args.Z, 1, method=oracle.LITERAL)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.sort(recs, args.Z, 1 + s, method=oracle.LITERAL)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = n / dt
+    sample = (f"each step: n=2^{args.cpu_sample_log2} 16-B records ({args.dist} u64 keys), Z={args.Z}, "
+              f"oracle (literal Algorithm 3.1 + in-bin permutation + std::stable_sort), one host thread")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"oblivious sort, n=2^{args.n_log2} 16-B records, Z={args.Z}",
+                       "sample_n": n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2008_01765_gb300 import _build
+    _build.build()
+    from paper_2008_01765_gb300 import bos, inputs
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n = 1 << args.n_log2
+    Z = args.Z
+    recs = inputs.make_records(n, REC, args.dist, seed=1 + rank)
+    host_in = torch.from_numpy(recs.view(np.uint8).reshape(-1))
+    x = host_in.to(dev)
+    del recs
+    out = torch.empty_like(x)
+    p = bos.params(REC, Z, seed=1)
+    ws = bos.alloc_workspace(bos.workspace_bytes(n, p), dev)
+    sh = bos._stream_handle(stream)
+
+    def step(seed, k=0):
+        p.seed = seed
+        p.k = k
+        return bos.sort_raw(x.data_ptr(), out.data_ptr(), n, p, ws.data_ptr(), ws.numel(), sh)
+
+    for w in range(args.warmup):
+        info = step(1000 + w)
+    torch.cuda.synchronize()
+    bos.profile_enable(True)
+    clocks = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        info = step(1 + s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(pg, ms, dev)
+    stats, launches = bos.profile_read()
+    bos.profile_enable(False)
+
+    value = world * n / (ms_max / 1e3)
+    hbm, peak_src = peaks()
+    # whole-step algorithmic bytes / step time
+    step_bytes = sum(v["bytes"] for v in stats.values()) / args.steps
+    top_name, top = max(((k, v) for k, v in stats.items()), key=lambda kv: kv[1]["ms"])
+    top_gbs = top["bytes"] / (top["ms"] / 1e3) / 1e9
+    workload = f"sort n=2^{args.n_log2} rec16 Z={Z}"
+    roof = {"bound": "hbm", "achieved": top_gbs, "peak": hbm, "unit": "GB/s", "frac": top_gbs / hbm,
+            "traffic": traffic_for(top_name, workload), "kernel": top_name,
+            "bytes_per_launch": top["bytes"] / top["launches"], "ms_per_launch": top["ms"] / top["launches"],
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s"}
+    kernels = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
+                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0}
+               for k, v in stats.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": workload, "n": n, "rec_bytes": REC, "Z": Z, "B": int(info.B),
+                       "L": int(info.L), "orp_passes": int(info.passes), "radix_passes": int(info.radix_passes),
+                       "keys": f"{args.dist} u64, payload = index", "l2": "inputs (16 GiB) larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_gbs": step_bytes / (ms / 1e3) / 1e9, "hbm_frac": step_bytes / (ms / 1e3) / 1e9 / hbm,
+            "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+            "clocks": clk}
+
+    # ---- end to end through the public API with host buffers (H2D + sort + D2H every step) ----
+    if not args.no_e2e:
+        pin_in = host_in.pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        for w in range(1):
+            x.copy_(pin_in, non_blocking=True)
+            step(2000 + w)
+            pin_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier(pg)
+        e0.record(stream)
+        ke = max(1, min(args.steps, 3))
+        for s in range(ke):
+            x.copy_(pin_in, non_blocking=True)
+            step(1 + s)
+            pin_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(pg, e0.elapsed_time(e1) / ke, dev)
+        line["e2e"] = {"value": world * n / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * REC,
+                       "d2h_bytes_per_step": n * REC, "ms_per_step": ems, "steps": ke}
+        del pin_in, pin_out
+
+    # ---- comparators: plain one-level-per-launch form, GPU bitonic sort (rank-local) ----
+    if not args.no_compare:
+        comp = {}
+        step(3000, k=1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(2):
+            pinfo = step(1 + s, k=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / 2
+        comp["plain_k1"] = {"value": n / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                            "orp_passes": int(pinfo.passes)}
+        del ws
+        torch.cuda.empty_cache()
+        bos.bitonic_sort(x, REC, out=out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(2):
+            bos.bitonic_sort(x, REC, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / 2
+        comp["bitonic"] = {"value": n / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
+        line["comparators"] = comp
+        line["speedup_vs_plain"] = pms / ms
+        line["speedup_vs_bitonic"] = bms / ms
+
+    if rank == 0 and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_sample_log2, Z, args.dist)
+        except Exception as e:  # pragma: no cover
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

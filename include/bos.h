@@ -1,0 +1,158 @@
+/*
+ * bos.h - C ABI of the GB300 bucket oblivious random permutation (ORP) and bucket oblivious
+ * sort library (libbos.so).
+ *
+ * The method is the one of Asharov, Chan, Nayak, Pass, Ren, Shi, "Bucket Oblivious Sort: An
+ * Extremely Simple Oblivious Sort" (SOSA 2020):
+ *   - Algorithm 3.1 (oblivious random bin assignment): every record gets a uniformly random
+ *     label in [0, B), the input is split evenly into B buckets of Z slots padded with dummies,
+ *     and log2 B butterfly levels of MergeSplit route each record to the bucket of its label.
+ *   - Section 3.2 (bucket ORP): the dummies are stripped, each final bucket is permuted at
+ *     random and the buckets are concatenated.
+ *   - Section 3.3 (bucket oblivious sort): the ORP output is sorted by a non-oblivious sort
+ *     (here a stable LSD radix sort on the key).
+ *
+ * Records are opaque blocks of rec_bytes bytes (8 or 16). The key is the unsigned little-endian
+ * integer of key_bytes bytes (4 for 8-byte records, 8 for 16-byte records) at offset 0; the
+ * rest of the record is payload and is never compared.
+ *
+ * Conventions for every entry point:
+ *   - Every pointer named d_* is a device pointer owned by the caller. The library never
+ *     allocates or frees memory, never prints and never aborts; it reports errors by status.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is stream-ordered.
+ *     bos_orp / bos_sort / bos_sort_batched synchronise `stream` once per attempt to read the
+ *     overflow flag (Algorithm 3.1, MergeSplit aborts on overflow; the call retries with a
+ *     fresh attempt counter, up to max_attempts).
+ *   - Results are a deterministic function of (input, n, Z, seed, rec_bytes, key_bytes) only:
+ *     they do not depend on k, on the block shape, on batching or on concurrency.
+ *   - d_out must not overlap d_in or the workspace (BOS_ERR_INVALID otherwise). n = 0 is a
+ *     no-op that returns BOS_OK.
+ */
+#ifndef BOS_H_
+#define BOS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BOS_OK = 0,
+  BOS_ERR_INVALID = 1,   /* bad argument (size, alignment, widths, aliasing, null pointer) */
+  BOS_ERR_OVERFLOW = 2,  /* every one of max_attempts attempts overflowed a bucket */
+  BOS_ERR_WORKSPACE = 3, /* ws_bytes smaller than bos_workspace_bytes() */
+  BOS_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+  BOS_ERR_TIMEOUT = 5    /* a bounded device-side wait gave up (the results are not valid) */
+} bos_status;
+
+/* flags */
+#define BOS_FLAG_NONE 0u
+/* Debug: report overflow for the first (flags >> 8) & 0xFF attempts, so the retry path runs
+ * without a tiny Z. The results are still those of the first attempt not forced to fail. */
+#define BOS_FLAG_FORCE_OVERFLOW(n) (((uint32_t)(n) & 0xFFu) << 8)
+/* Debug: one look-back producer skips its publish, so the bounded wait must time out and the
+ * call must return BOS_ERR_TIMEOUT (tests the failure path without hanging a GPU). */
+#define BOS_FLAG_SKIP_PUBLISH 0x1u
+
+typedef struct {
+  uint32_t rec_bytes;    /* 8 or 16 */
+  uint32_t key_bytes;    /* 4 (rec 8) or 8 (rec 16) */
+  uint32_t Z;            /* bucket size, 2 <= Z <= 4096 for 8-byte and <= 2048 for 16-byte records
+                            (one bucket pair must fit in shared memory); Section 3.4 suggests 512 */
+  uint32_t k;            /* butterfly levels fused per HBM pass; 0 = automatic, 1 = plain form
+                            (one launch per level). Never changes the result. */
+  uint32_t max_attempts; /* overflow retries; 0 = default (8) */
+  uint32_t flags;        /* BOS_FLAG_* */
+  uint64_t seed;         /* Philox key of the labels and of the in-bin permutation */
+} bos_params;
+
+typedef struct {
+  uint32_t attempts; /* attempts run (1 unless an overflow forced a retry) */
+  uint32_t L;        /* log2 B, the number of butterfly levels */
+  uint32_t passes;   /* HBM passes of the ORP in the last attempt */
+  uint32_t radix_passes; /* LSD radix passes run by the sort (digits where all keys agree are skipped) */
+  uint64_t B;        /* number of buckets: smallest power of two with B * Z >= 2n */
+} bos_info;
+
+/* Bytes of device workspace bos_orp / bos_sort need for n records under *p (0 for n = 0).
+ * Returns 0 and sets nothing on invalid parameters. */
+size_t bos_workspace_bytes(uint64_t n, const bos_params* p);
+
+/* Bucket ORP (Algorithm 3.1 + Section 3.2): d_out[0..n) = d_in permuted uniformly at random
+ * (determined by p->seed). d_in: n * rec_bytes bytes, read only, aligned to rec_bytes. d_out: n *
+ * rec_bytes bytes, aligned to rec_bytes. d_ws: ws_bytes >= bos_workspace_bytes(n, p), 256-byte
+ * aligned; its contents on entry do not matter. info may be NULL. */
+bos_status bos_orp(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,
+                   size_t ws_bytes, void* stream, bos_info* info);
+
+/* Bucket oblivious sort (Section 3.3): the ORP of d_in followed by a stable ascending LSD radix
+ * sort on the key, so equal keys keep their ORP order. Same arguments as bos_orp. */
+bos_status bos_sort(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,
+                    size_t ws_bytes, void* stream, bos_info* info);
+
+/* Batched ORP / sort of `num` independent arrays stored back to back (spec batching; the
+ * paper has no batched form). Array j occupies records [h_offsets[j], h_offsets[j+1]) of d_in
+ * and of d_out, is processed with seed h_seeds[j], Z = h_Z[j] (or base->Z when h_Z is NULL)
+ * and op h_ops[j] (0 = ORP, 1 = sort). Its result equals bos_orp / bos_sort of that array alone.
+ * h_attempts (nullable, num entries) receives the attempts of each array. Host arrays are read
+ * during the call only. */
+size_t bos_batched_workspace_bytes(const uint64_t* h_offsets, uint32_t num, const uint32_t* h_Z,
+                                   const bos_params* base);
+bos_status bos_sort_batched(const void* d_in, void* d_out, const uint64_t* h_offsets,
+                            uint32_t num, const uint64_t* h_seeds, const uint32_t* h_Z,
+                            const uint8_t* h_ops, const bos_params* base, void* d_ws,
+                            size_t ws_bytes, void* stream, uint32_t* h_attempts);
+
+/* GPU bitonic sorting network (Table 1's comparator; not oblivious-sort output compatible:
+ * equal keys are ordered by payload). n must be a power of two (BOS_ERR_INVALID otherwise).
+ * Sorts d_in into d_out by (key, payload) ascending. Needs no workspace. */
+bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t rec_bytes,
+                            uint32_t key_bytes, void* stream);
+
+/* Debug address trace (obliviousness check, Section 3.1 and Lemma 3.3). While attached, every
+ * global-memory access of the ORP kernels is appended to d_buf as two uint64 words
+ * {(kind << 56) | (buffer << 48) | bytes, byte offset within that buffer}; word 0 of d_buf
+ * counts the entries written (entries beyond the buffer's capacity are counted, not stored).
+ * kind: 1 = read, 2 = write. buffer: 0 = input, 1 = slot records A, 2 = slot tags A,
+ * 3 = slot records B, 4 = slot tags B, 5 = output. Attach NULL to detach. The trace run uses
+ * separate kernel instances; the results are identical. */
+bos_status bos_trace_attach(void* d_buf, size_t bytes);
+
+/* Self-test hook for the random source (Philox4x32-10, Salmon et al. SC 2011) that draws the
+ * labels of Algorithm 3.1 and the in-bin permutation keys of Section 3.2. For i < n it writes
+ * the library's Philox of counter d_ctr[4i..4i+3] and key d_key[2i..2i+1] to d_out[4i..4i+3],
+ * and, when d_out_curand is not NULL, cuRAND's curand_Philox4x32_10 of the same inputs to
+ * d_out_curand. All buffers are device memory owned by the caller. */
+bos_status bos_selftest_philox(const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out,
+                               uint32_t* d_out_curand, uint64_t n, void* stream);
+
+/* Kernel timing for benchmarks (no counterpart in the paper). While enabled, every launch of
+ * bos_orp / bos_sort / bos_bitonic_sort is bracketed by CUDA events recorded on the call's
+ * stream; each kernel class accumulates its launches, device milliseconds and algorithmic bytes
+ * (whole slot arrays read and written by a butterfly pass; records read and written by a radix
+ * pass; keys read by the histogram). bos_profile_enable creates its events on the first call
+ * (CUDA events, no device memory) and resets the totals; not thread-safe. */
+typedef struct {
+  char name[32];     /* orp_pass_first, orp_pass_mid, orp_pass_last, orp_pass_single, radix_hist,
+                        radix_prep, radix_pass, radix_pass_skipped, bitonic */
+  uint32_t launches;
+  double ms;         /* summed device time */
+  double bytes;      /* summed algorithmic bytes */
+} bos_kernel_stat;
+bos_status bos_profile_enable(int on);
+/* Fills up to max entries (classes with at least one launch); *total_launches (nullable) gets the
+ * number of kernel launches counted since the last enable. Returns the entries written. */
+uint32_t bos_profile_read(bos_kernel_stat* out, uint32_t max, uint64_t* total_launches);
+
+const char* bos_status_str(bos_status s);
+
+/* Library version, (major << 16) | minor. */
+uint32_t bos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOS_H_ */

@@ -44,6 +44,9 @@ def lib():
         L.or_orp.argtypes = [_vp, _vp, _u64, _u32, _u32, _u64, _u32, ctypes.c_int,
                              ctypes.POINTER(OrpInfo), _vp, _vp, _u64, ctypes.POINTER(_u64)]
         L.or_orp.restype = ctypes.c_int
+        L.or_orp_from.argtypes = [_vp, _vp, _u64, _u32, _u32, _u64, _u32, _u32, ctypes.c_int,
+                                  ctypes.POINTER(OrpInfo), _vp, _vp, _u64, ctypes.POINTER(_u64)]
+        L.or_orp_from.restype = ctypes.c_int
         L.or_orp_many.argtypes = [_vp, _vp, _u64, _u32, _u32, _u64, _u64, _u32, ctypes.c_int, _vp]
         L.or_orp_many.restype = ctypes.c_int
         L.or_stable_sort.argtypes = [_vp, _u64, _u32, _u32]
@@ -113,7 +116,8 @@ def overflow_count(n, Z, seed0, nseeds, attempt=0, method=CLOSED):
     return int(lib().or_overflow_count(n, Z, seed0, nseeds, attempt, method))
 
 
-def orp(recs, Z, seed, max_attempts=8, method=LITERAL, want_loads=False, trace_cap=0):
+def orp(recs, Z, seed, max_attempts=8, method=LITERAL, want_loads=False, trace_cap=0,
+        first_attempt=0):
     """Bucket ORP of a structured record array. Returns (out, info[, loads][, trace])."""
     recs = np.ascontiguousarray(recs)
     n = recs.shape[0]
@@ -123,9 +127,11 @@ def orp(recs, Z, seed, max_attempts=8, method=LITERAL, want_loads=False, trace_c
     loads = np.zeros(B, dtype=np.uint32) if want_loads else None
     trace = np.zeros(trace_cap, dtype=np.uint64) if trace_cap else None
     tlen = _u64(0)
-    st = lib().or_orp(_ptr(recs), _ptr(out), n, _rec_bytes(recs), Z, seed, max_attempts, method,
-                      ctypes.byref(info), _ptr(loads) if loads is not None else None,
-                      _ptr(trace) if trace is not None else None, trace_cap, ctypes.byref(tlen))
+    st = lib().or_orp_from(_ptr(recs), _ptr(out), n, _rec_bytes(recs), Z, seed, first_attempt,
+                           max_attempts, method, ctypes.byref(info),
+                           _ptr(loads) if loads is not None else None,
+                           _ptr(trace) if trace is not None else None, trace_cap,
+                           ctypes.byref(tlen))
     if st != OK:
         raise OracleError(st)
     res = [out, info]
@@ -162,9 +168,12 @@ def radix_sort(recs):
     return r
 
 
-def sort(recs, Z, seed, max_attempts=8, method=LITERAL, sorter=0):
+def sort(recs, Z, seed, max_attempts=8, method=LITERAL, sorter=0, first_attempt=0):
     """Bucket oblivious sort: ORP, then a stable sort by key. Returns (out, info)."""
     recs = np.ascontiguousarray(recs)
+    if first_attempt:
+        out, info = orp(recs, Z, seed, max_attempts, method, first_attempt=first_attempt)
+        return (radix_sort(out) if sorter == 1 else stable_sort(out)), info
     out = np.zeros_like(recs)
     info = OrpInfo()
     st = lib().or_sort(_ptr(recs), _ptr(out), recs.shape[0], _rec_bytes(recs), _key_bytes(recs),

@@ -323,12 +323,14 @@ uint64_t or_overflow_count(uint64_t n, uint32_t Z, uint64_t seed0, uint64_t nsee
 }
 
 // Bucket ORP (Section 3.2) of n records of rec_bytes each. method 0 runs the literal
-// Algorithm 3.1; method 1 its closed form. `loads` (nullable, B entries) receives the final
+// Algorithm 3.1; method 1 its closed form. Attempts first_attempt .. max_attempts-1 are tried
+// in order (or_orp starts at attempt 0). `loads` (nullable, B entries) receives the final
 // bucket loads; `trace` (nullable) receives the literal run's access trace of the successful
 // attempt (trace_len gets the full length even if it exceeds trace_cap).
-int or_orp(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z, uint64_t seed,
-           uint32_t max_attempts, int method, OrpInfo* info, uint32_t* loads, uint64_t* trace,
-           uint64_t trace_cap, uint64_t* trace_len) {
+int or_orp_from(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z,
+                uint64_t seed, uint32_t first_attempt, uint32_t max_attempts, int method,
+                OrpInfo* info, uint32_t* loads, uint64_t* trace, uint64_t trace_cap,
+                uint64_t* trace_len) {
   if (Z < 1 || (rec_bytes != 8 && rec_bytes != 16) || max_attempts < 1) return OR_ERR_INVALID;
   uint64_t B;
   uint32_t L;
@@ -337,7 +339,7 @@ int or_orp(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z
     info->B = B;
     info->L = L;
   }
-  for (uint32_t a = 0; a < max_attempts; ++a) {
+  for (uint32_t a = first_attempt; a < max_attempts; ++a) {
     std::vector<Slot> fin;
     Counters cnt;
     Tracer tr;
@@ -358,6 +360,13 @@ int or_orp(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z
   }
   if (info) info->attempts = max_attempts;
   return OR_ERR_OVERFLOW;
+}
+
+int or_orp(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z, uint64_t seed,
+           uint32_t max_attempts, int method, OrpInfo* info, uint32_t* loads, uint64_t* trace,
+           uint64_t trace_cap, uint64_t* trace_len) {
+  return or_orp_from(in, out, n, rec_bytes, Z, seed, 0, max_attempts, method, info, loads, trace,
+                     trace_cap, trace_len);
 }
 
 // ORP of one small array under `count` consecutive seeds; out receives count * n records.

@@ -1,0 +1,242 @@
+"""ctypes binding of libbos.so (the C ABI declared in include/bos.h).
+
+Argument marshalling only: every step of the ORP and the sort runs in the library's CUDA
+kernels. PyTorch provides device memory and streams. There is no CPU fallback: if libbos.so
+cannot be loaded the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbos.so")
+
+OK, ERR_INVALID, ERR_OVERFLOW, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(6)
+FLAG_SKIP_PUBLISH = 0x1
+
+
+def FLAG_FORCE_OVERFLOW(n):
+    return (n & 0xFF) << 8
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("rec_bytes", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
+                ("Z", ctypes.c_uint32), ("k", ctypes.c_uint32), ("max_attempts", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("attempts", ctypes.c_uint32), ("L", ctypes.c_uint32), ("passes", ctypes.c_uint32),
+                ("radix_passes", ctypes.c_uint32), ("B", ctypes.c_uint64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint32),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class BosError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+
+
+def lib():
+    """Load libbos.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbos.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.bos_workspace_bytes.argtypes = [_u64, ctypes.POINTER(Params)]
+        L.bos_workspace_bytes.restype = ctypes.c_size_t
+        for name in ("bos_orp", "bos_sort"):
+            f = getattr(L, name)
+            f.argtypes = [_vp, _vp, _u64, ctypes.POINTER(Params), _vp, ctypes.c_size_t, _vp,
+                          ctypes.POINTER(Info)]
+            f.restype = ctypes.c_int
+        L.bos_batched_workspace_bytes.argtypes = [_vp, _u32, _vp, ctypes.POINTER(Params)]
+        L.bos_batched_workspace_bytes.restype = ctypes.c_size_t
+        L.bos_sort_batched.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp, ctypes.POINTER(Params),
+                                       _vp, ctypes.c_size_t, _vp, _vp]
+        L.bos_sort_batched.restype = ctypes.c_int
+        L.bos_bitonic_sort.argtypes = [_vp, _vp, _u64, _u32, _u32, _vp]
+        L.bos_bitonic_sort.restype = ctypes.c_int
+        L.bos_trace_attach.argtypes = [_vp, ctypes.c_size_t]
+        L.bos_trace_attach.restype = ctypes.c_int
+        L.bos_status_str.argtypes = [ctypes.c_int]
+        L.bos_status_str.restype = ctypes.c_char_p
+        L.bos_version.restype = _u32
+        L.bos_selftest_philox.argtypes = [_vp, _vp, _vp, _vp, _u64, _vp]
+        L.bos_selftest_philox.restype = ctypes.c_int
+        L.bos_profile_enable.argtypes = [ctypes.c_int]
+        L.bos_profile_enable.restype = ctypes.c_int
+        L.bos_profile_read.argtypes = [ctypes.POINTER(KernelStat), _u32, ctypes.POINTER(_u64)]
+        L.bos_profile_read.restype = _u32
+        _lib = L
+    return _lib
+
+
+def status_str(s):
+    return lib().bos_status_str(int(s)).decode()
+
+
+def params(rec_bytes=16, Z=512, seed=1, k=0, max_attempts=0, flags=0):
+    return Params(rec_bytes, 4 if rec_bytes == 8 else 8, Z, k, max_attempts, flags, seed)
+
+
+def workspace_bytes(n, p: Params) -> int:
+    return int(lib().bos_workspace_bytes(n, ctypes.byref(p)))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(st, what):
+    if st != OK:
+        raise BosError(st, what)
+
+
+def alloc_workspace(nbytes, device="cuda"):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def orp_raw(d_in, d_out, n, p: Params, ws, ws_bytes, stream_handle) -> Info:
+    """bos_orp on raw device pointers (ints); returns Info, raises BosError."""
+    info = Info()
+    st = lib().bos_orp(_vp(d_in), _vp(d_out), n, ctypes.byref(p), _vp(ws), ws_bytes,
+                       stream_handle, ctypes.byref(info))
+    _check(st, "bos_orp")
+    return info
+
+
+def sort_raw(d_in, d_out, n, p: Params, ws, ws_bytes, stream_handle) -> Info:
+    info = Info()
+    st = lib().bos_sort(_vp(d_in), _vp(d_out), n, ctypes.byref(p), _vp(ws), ws_bytes,
+                        stream_handle, ctypes.byref(info))
+    _check(st, "bos_sort")
+    return info
+
+
+def _run(fn, x, out, n, rec_bytes, Z, seed, k, max_attempts, flags, workspace, stream):
+    import torch
+    p = params(rec_bytes, Z, seed, k, max_attempts, flags)
+    if out is None:
+        out = torch.empty_like(x)
+    need = workspace_bytes(n, p)
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need, x.device)
+    info = fn(x.data_ptr(), out.data_ptr(), n, p, workspace.data_ptr(), workspace.numel(),
+              _stream_handle(stream))
+    return out, info
+
+
+def orp(x, rec_bytes, Z=512, seed=1, k=0, max_attempts=0, flags=0, out=None, workspace=None,
+        stream=None):
+    """Bucket ORP of a contiguous CUDA tensor holding n records of rec_bytes bytes each."""
+    n = x.numel() * x.element_size() // rec_bytes
+    return _run(orp_raw, x, out, n, rec_bytes, Z, seed, k, max_attempts, flags, workspace, stream)
+
+
+def sort(x, rec_bytes, Z=512, seed=1, k=0, max_attempts=0, flags=0, out=None, workspace=None,
+         stream=None):
+    """Bucket oblivious sort of a contiguous CUDA tensor of records."""
+    n = x.numel() * x.element_size() // rec_bytes
+    return _run(sort_raw, x, out, n, rec_bytes, Z, seed, k, max_attempts, flags, workspace, stream)
+
+
+def bitonic_sort(x, rec_bytes, out=None, stream=None):
+    import torch
+    n = x.numel() * x.element_size() // rec_bytes
+    if out is None:
+        out = torch.empty_like(x)
+    st = lib().bos_bitonic_sort(_vp(x.data_ptr()), _vp(out.data_ptr()), n, rec_bytes,
+                                4 if rec_bytes == 8 else 8, _stream_handle(stream))
+    _check(st, "bos_bitonic_sort")
+    return out
+
+
+def batched_workspace_bytes(offsets, Zs, base: Params):
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    z = None if Zs is None else np.ascontiguousarray(Zs, dtype=np.uint32)
+    return int(lib().bos_batched_workspace_bytes(off.ctypes.data_as(_vp), off.size - 1,
+                                                 None if z is None else z.ctypes.data_as(_vp),
+                                                 ctypes.byref(base)))
+
+
+def sort_batched(x, out, offsets, seeds, ops, base: Params, Zs=None, workspace=None, stream=None):
+    """Batched ORP/sort of back-to-back arrays; returns the attempts per array."""
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    op = np.ascontiguousarray(ops, dtype=np.uint8)
+    z = None if Zs is None else np.ascontiguousarray(Zs, dtype=np.uint32)
+    num = off.size - 1
+    need = batched_workspace_bytes(off, z, base)
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need, x.device)
+    att = np.zeros(max(num, 1), dtype=np.uint32)
+    st = lib().bos_sort_batched(_vp(x.data_ptr()), _vp(out.data_ptr()), off.ctypes.data_as(_vp),
+                                num, sd.ctypes.data_as(_vp), z.ctypes.data_as(_vp) if z is not None
+                                else None, op.ctypes.data_as(_vp), ctypes.byref(base),
+                                _vp(workspace.data_ptr()), workspace.numel(),
+                                _stream_handle(stream), att.ctypes.data_as(_vp))
+    _check(st, "bos_sort_batched")
+    return att[:num]
+
+
+def trace_attach(buf):
+    """Attach a uint8/uint64 CUDA tensor as the address-trace buffer (None detaches)."""
+    if buf is None:
+        _check(lib().bos_trace_attach(None, 0), "bos_trace_attach")
+    else:
+        _check(lib().bos_trace_attach(_vp(buf.data_ptr()), buf.numel() * buf.element_size()),
+               "bos_trace_attach")
+
+
+def selftest_philox(ctr, key, with_curand=True, stream=None):
+    """Library Philox (and cuRAND's) of CUDA uint32 tensors ctr (n,4) and key (n,2)."""
+    import torch
+    n = ctr.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    ref = torch.empty_like(out) if with_curand else None
+    st = lib().bos_selftest_philox(_vp(ctr.data_ptr()), _vp(key.data_ptr()), _vp(out.data_ptr()),
+                                   _vp(ref.data_ptr()) if ref is not None else None, n,
+                                   _stream_handle(stream))
+    _check(st, "bos_selftest_philox")
+    return out, ref
+
+
+def profile_enable(on=True):
+    _check(lib().bos_profile_enable(1 if on else 0), "bos_profile_enable")
+
+
+def profile_read():
+    """{kernel class: {launches, ms, bytes}} and the total launch count since enable."""
+    arr = (KernelStat * 16)()
+    tot = _u64(0)
+    m = lib().bos_profile_read(arr, 16, ctypes.byref(tot))
+    stats = {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].ms),
+                                    "bytes": float(arr[i].bytes)} for i in range(m)}
+    return stats, int(tot.value)
+
+
+# ---- numpy <-> torch helpers for structured record arrays ----
+def to_device(recs: np.ndarray, device="cuda"):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(recs).view(np.uint8).reshape(-1)).to(device)
+
+
+def to_host(t, dtype) -> np.ndarray:
+    return t.cpu().numpy().view(dtype)

@@ -1,0 +1,173 @@
+// Shared device helpers of the CUDA path: Philox4x32-10, record types, bounded look-back
+// waits and the debug address trace. sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bos {
+
+constexpr uint32_t kDummy = 0xFFFFFFFFu;  // tag of a dummy slot; real tags are labels < 2^31
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011). Ten rounds; each multiplies counter words 0 and 2 by
+// the two round multipliers, xors the high halves into words 1 and 3 with the round key, and
+// bumps the key by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------------------------
+struct PhiloxOut {
+  uint32_t w0, w1, w2, w3;
+};
+
+__host__ __device__ __forceinline__ PhiloxOut philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                            uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+#ifdef __CUDA_ARCH__
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+#else
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+
+// Philox block at position `index` of stream `stream` for attempt `attempt`:
+// counter = (lo index, hi index, attempt, stream), key = (lo seed, hi seed).
+__host__ __device__ __forceinline__ PhiloxOut philox_at(uint64_t index, uint32_t attempt,
+                                                        uint32_t stream, uint64_t seed) {
+  return philox4x32_10((uint32_t)index, (uint32_t)(index >> 32), attempt, stream, (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
+// Label of element i: top L bits of word 0 of stream 0 (Algorithm 3.1, random key in [0, B)).
+__device__ __forceinline__ uint32_t label_of(uint64_t i, uint64_t seed, uint32_t attempt, uint32_t L) {
+  if (L == 0) return 0;
+  return philox_at(i, attempt, 0, seed).w0 >> (32 - L);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Records: 8-byte {u32 key, u32 payload} as uint2, 16-byte {u64 key, u64 payload} as uint4.
+// ---------------------------------------------------------------------------------------------
+template <int R> struct RecT;
+template <> struct RecT<8> {
+  using T = uint2;
+  using Key = uint32_t;
+  static constexpr int kDigits = 4;
+  __device__ __forceinline__ static Key key(const T& r) { return r.x; }
+  __device__ __forceinline__ static T zero() { return make_uint2(0, 0); }
+};
+template <> struct RecT<16> {
+  using T = uint4;
+  using Key = unsigned long long;
+  static constexpr int kDigits = 8;
+  __device__ __forceinline__ static Key key(const T& r) {
+    return (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+  }
+  __device__ __forceinline__ static T zero() { return make_uint4(0, 0, 0, 0); }
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Control block at the start of the workspace (zeroed at the start of every attempt).
+// ---------------------------------------------------------------------------------------------
+struct Ctrl {
+  uint32_t overflow;         // any MergeSplit output received more than Z reals
+  uint32_t timeout;          // a bounded wait gave up
+  uint32_t forced;           // debug: attempts still to be reported as overflowed
+  uint32_t radix_live;       // bit d set: digit d of the keys is not constant (a radix pass runs)
+  uint32_t tickets[60];      // dynamic work counters, one per launch that orders its CTAs
+};
+static_assert(sizeof(Ctrl) == 256, "control block size");
+
+// Bounded spin: number of polls before a wait gives up (~0.5 s with the back-off below).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Look-back status word: bits 62..63 = state (1 aggregate, 2 inclusive prefix), bits 56..61 =
+// tag of the launch that wrote it (so one zeroed array serves several passes), bits 0..55 value.
+constexpr unsigned long long kStAgg = 1ull << 62;
+constexpr unsigned long long kStIncl = 2ull << 62;
+constexpr unsigned long long kStValue = (1ull << 56) - 1;
+
+__device__ __forceinline__ unsigned long long st_word(unsigned long long state, uint32_t tag,
+                                                      unsigned long long value) {
+  return state | ((unsigned long long)(tag & 63u) << 56) | (value & kStValue);
+}
+
+// Exclusive prefix of tile `tile` over its predecessors (decoupled look-back, one thread). The
+// word of tile j is status[j * stride]. Spins with a limit; on timeout raises ctrl->timeout and
+// returns the prefix gathered so far.
+__device__ __forceinline__ unsigned long long lookback(const unsigned long long* status, uint64_t tile,
+                                                       uint64_t stride, uint32_t tag, Ctrl* ctrl) {
+  unsigned long long prefix = 0;
+  int64_t j = (int64_t)tile - 1;
+  while (j >= 0) {
+    unsigned long long w = 0;
+    uint32_t spins = 0;
+    while (true) {
+      w = ld_acquire_u64(status + (uint64_t)j * stride);
+      if ((w >> 62) != 0 && ((w >> 56) & 63u) == tag) break;
+      if (++spins > kSpinLimit) {
+        atomicExch(&ctrl->timeout, 1u);
+        return prefix;
+      }
+      if (spins > 32) __nanosleep(64);
+    }
+    prefix += w & kStValue;
+    if (w & kStIncl) break;
+    --j;
+  }
+  return prefix;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Debug address trace: {(kind << 56) | (buffer << 48) | bytes, byte offset}.
+// ---------------------------------------------------------------------------------------------
+enum TraceBuf : uint32_t {
+  kBufIn = 0, kBufRecA = 1, kBufTagA = 2, kBufRecB = 3, kBufTagB = 4, kBufOut = 5, kBufTmp = 6
+};
+enum TraceKind : uint32_t { kRead = 1, kWrite = 2 };
+
+struct Trace {
+  unsigned long long* buf;  // word 0 = entry counter; entries start at word 2
+  unsigned long long cap;   // entries that fit
+};
+
+template <bool TRACE>
+__device__ __forceinline__ void trace_log(const Trace& tr, uint32_t kind, uint32_t buffer,
+                                          uint32_t bytes, uint64_t offset) {
+  if constexpr (TRACE) {
+    const unsigned long long e = atomicAdd(tr.buf, 1ull);
+    if (e < tr.cap) {
+      tr.buf[2 + 2 * e] = ((unsigned long long)kind << 56) | ((unsigned long long)buffer << 48) | bytes;
+      tr.buf[3 + 2 * e] = offset;
+    }
+  }
+}
+
+}  // namespace bos

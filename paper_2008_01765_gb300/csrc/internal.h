@@ -1,0 +1,57 @@
+// Internal interfaces between the host orchestration (api.cu) and the kernel files.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bos {
+
+constexpr int kModeFirst = 1;
+constexpr int kModeLast = 2;
+
+struct PassArgs {
+  const void* in;           // FIRST: input records
+  const void* in_rec;       // otherwise: slot records of the previous array
+  const uint32_t* in_tag;   // otherwise: slot tags of the previous array
+  void* out_rec;            // not LAST: slot records of the next array
+  uint32_t* out_tag;        // not LAST: slot tags of the next array
+  void* out0;               // LAST: output records
+  void* out1;               // LAST: alternate output (sort scratch), see out_sel
+  uint32_t out_sel;         // LAST: 1 = write out1 when an odd number of radix passes will run
+  uint32_t skip_publish;    // debug: subproblem 0 of the LAST pass never publishes
+  uint64_t n, B;
+  uint32_t Z, L, i, k, attempt, ticket_slot;
+  uint64_t seed;
+  Ctrl* ctrl;
+  unsigned long long* status;  // LAST: look-back words, one per subproblem
+  uint32_t buf_in_rec, buf_in_tag, buf_out_rec, buf_out_tag;  // trace buffer ids
+  Trace trace;
+};
+
+uint32_t orp_smem_bytes(int R, uint32_t Z, uint32_t k, bool last);
+cudaError_t launch_orp_pass(const PassArgs& a, int mode, uint64_t grid, cudaStream_t st, int R,
+                            bool trace);
+
+// LSD radix sort (radix.cu)
+struct RadixArgs {
+  const void* in;                 // histogram source (any order of the same multiset)
+  void* buf0;                     // final output
+  void* buf1;                     // scratch of n records
+  uint64_t n;
+  uint32_t* hist;                 // [digits][256]
+  unsigned long long* dbase;      // [digits][256] exclusive digit offsets
+  unsigned long long* status;     // [tiles][256] look-back words
+  Ctrl* ctrl;
+  uint32_t ticket_base;
+};
+uint64_t radix_tiles(uint64_t n, int R);
+cudaError_t launch_radix_hist(const RadixArgs& a, int R, cudaStream_t st);
+cudaError_t launch_radix_prep(const RadixArgs& a, int R, cudaStream_t st);
+cudaError_t launch_radix_pass(const RadixArgs& a, int R, uint32_t digit, cudaStream_t st);
+
+// Bitonic comparator (bitonic.cu)
+cudaError_t launch_bitonic(const void* in, void* out, uint64_t n, int R, cudaStream_t st);
+
+}  // namespace bos

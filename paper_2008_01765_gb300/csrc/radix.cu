@@ -1,0 +1,219 @@
+// Stable LSD radix sort on the record key (the non-oblivious sort of Section 3.3), sm_103a.
+//
+// Onesweep organisation: one histogram pass gives the counts of all 8-bit digits at once; each
+// digit then takes one pass that ranks a tile of records stably per digit (warp match + per-warp
+// counters), finds the tile's global offset per digit by decoupled look-back over the tiles in
+// ticket order, stages the tile in shared memory in digit order and writes it out in runs.
+// A digit on which every key agrees is skipped (the pass would be the identity); the buffers
+// alternate so that the last pass that runs writes the final output.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bos {
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;
+constexpr uint32_t kTile = kThreads * kItems;
+constexpr int kHistCtas = 4 * 152;
+
+template <int R>
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(RadixArgs a) {
+  using Rec = typename RecT<R>::T;
+  constexpr int D = RecT<R>::kDigits;
+  __shared__ uint32_t h[D][256];
+  for (int x = threadIdx.x; x < D * 256; x += kThreads) (&h[0][0])[x] = 0;
+  __syncthreads();
+  const Rec* in = reinterpret_cast<const Rec*>(a.in);
+  for (uint64_t idx = (uint64_t)blockIdx.x * kThreads + threadIdx.x; idx < a.n;
+       idx += (uint64_t)gridDim.x * kThreads) {
+    const auto key = RecT<R>::key(in[idx]);
+#pragma unroll
+    for (int d = 0; d < D; ++d) atomicAdd(&h[d][(key >> (8 * d)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < D * 256; x += kThreads) {
+    const uint32_t c = (&h[0][0])[x];
+    if (c) atomicAdd(a.hist + x, c);
+  }
+}
+
+// Per digit: exclusive offsets of the 256 digit values, and whether the digit is live.
+template <int R>
+__global__ void __launch_bounds__(256) radix_prep_kernel(RadixArgs a) {
+  __shared__ uint32_t s[256];
+  __shared__ uint32_t any_full;
+  const int d = blockIdx.x, v = threadIdx.x;
+  const uint32_t c = a.hist[d * 256 + v];
+  s[v] = c;
+  if (v == 0) any_full = 0;
+  __syncthreads();
+  if ((uint64_t)c == a.n) any_full = 1;
+  // inclusive scan (Hillis-Steele)
+  for (int o = 1; o < 256; o <<= 1) {
+    const uint32_t y = v >= o ? s[v - o] : 0;
+    __syncthreads();
+    s[v] += y;
+    __syncthreads();
+  }
+  a.dbase[d * 256 + v] = s[v] - c;
+  if (v == 0 && !any_full) atomicOr(&a.ctrl->radix_live, 1u << d);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads) radix_pass_kernel(RadixArgs a, uint32_t digit) {
+  using Rec = typename RecT<R>::T;
+  const uint32_t live = a.ctrl->radix_live;
+  if (!((live >> digit) & 1u)) return;
+  // Buffer chain: X_nlive = buf0 (output); X_j alternates backwards. This pass maps X_c -> X_c+1.
+  const uint32_t nlive = __popc(live);
+  const uint32_t c = __popc(live & ((1u << digit) - 1));
+  auto X = [&](uint32_t j) -> Rec* {
+    return reinterpret_cast<Rec*>(((nlive - j) & 1) ? a.buf1 : a.buf0);
+  };
+  const Rec* src = X(c);
+  Rec* dst = X(c + 1);
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  Rec* stage = reinterpret_cast<Rec*>(smem);                                   // [kTile]
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + kTile * sizeof(Rec));    // [kWarps][257]
+  uint32_t* lstart = wcnt + kWarps * 257;                                      // [257]
+  unsigned long long* gstart = reinterpret_cast<unsigned long long*>(lstart + 258);  // [256]
+  uint32_t* misc = reinterpret_cast<uint32_t*>(gstart + 256);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) misc[0] = atomicAdd(&a.ctrl->tickets[a.ticket_base + digit], 1u);
+  for (int x = tid; x < kWarps * 257; x += kThreads) wcnt[x] = 0;
+  __syncthreads();
+  const uint64_t tile = misc[0];
+  const uint64_t t0 = tile * kTile;
+  const uint32_t shift = 8 * digit;
+  const uint32_t lt_mask = lanemask_lt();
+
+  Rec rc[kItems];
+  uint32_t dg[kItems], rk[kItems];
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const uint64_t idx = t0 + warp * 32 * kItems + it * 32 + lane;
+    dg[it] = 256;
+    if (idx < a.n) {
+      rc[it] = src[idx];
+      dg[it] = (uint32_t)(RecT<R>::key(rc[it]) >> shift) & 255u;
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg[it]);
+    const uint32_t lt = __popc(peers & lt_mask);
+    rk[it] = wcnt[warp * 257 + dg[it]] + lt;
+    __syncwarp();
+    if (lt == 0) wcnt[warp * 257 + dg[it]] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit value: tile count, exclusive offsets over warps
+  uint32_t cnt = 0;
+  if (tid < 256) {
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t x = wcnt[w * 257 + tid];
+      wcnt[w * 257 + tid] = cnt;
+      cnt += x;
+    }
+    unsigned long long* st = a.status + tile * 256 + tid;
+    const uint32_t tag = digit + 1;
+    if (tile == 0) {
+      st_release_u64(st, st_word(kStIncl, tag, cnt));
+      gstart[tid] = a.dbase[digit * 256 + tid];
+    } else {
+      st_release_u64(st, st_word(kStAgg, tag, cnt));
+      const unsigned long long pre = lookback(a.status + tid, tile, 256, tag, a.ctrl);
+      st_release_u64(st, st_word(kStIncl, tag, pre + cnt));
+      gstart[tid] = a.dbase[digit * 256 + tid] + pre;
+    }
+    lstart[tid] = cnt;
+  }
+  __syncthreads();
+  // exclusive scan of the 256 tile counts (warp 0..7 hold them; simple serial-in-warp scan)
+  if (warp == 0) {
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[e] = lstart[lane * 8 + e];
+      sum += v[e];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      lstart[lane * 8 + e] = run;
+      run += v[e];
+    }
+    if (lane == 31) lstart[256] = run;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    if (dg[it] < 256) stage[lstart[dg[it]] + wcnt[warp * 257 + dg[it]] + rk[it]] = rc[it];
+  }
+  __syncthreads();
+  const uint32_t total = lstart[256];
+  for (uint32_t j = tid; j < total; j += kThreads) {
+    const Rec r = stage[j];
+    const uint32_t v = (uint32_t)(RecT<R>::key(r) >> shift) & 255u;
+    const uint64_t pos = gstart[v] + (j - lstart[v]);
+    if (pos < a.n) dst[pos] = r;
+  }
+}
+
+template <int R>
+uint32_t pass_smem() {
+  using Rec = typename RecT<R>::T;
+  return kTile * sizeof(Rec) + (kWarps * 257 + 258) * 4 + 256 * 8 + 64;
+}
+
+}  // namespace
+
+uint64_t radix_tiles(uint64_t n, int) { return (n + kTile - 1) / kTile; }
+
+cudaError_t launch_radix_hist(const RadixArgs& a, int R, cudaStream_t st) {
+  const uint64_t need = (a.n + kThreads - 1) / kThreads;
+  const unsigned grid = (unsigned)(need < (uint64_t)kHistCtas ? (need ? need : 1) : kHistCtas);
+  if (R == 8)
+    radix_hist_kernel<8><<<grid, kThreads, 0, st>>>(a);
+  else
+    radix_hist_kernel<16><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radix_prep(const RadixArgs& a, int R, cudaStream_t st) {
+  if (R == 8)
+    radix_prep_kernel<8><<<RecT<8>::kDigits, 256, 0, st>>>(a);
+  else
+    radix_prep_kernel<16><<<RecT<16>::kDigits, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radix_pass(const RadixArgs& a, int R, uint32_t digit, cudaStream_t st) {
+  const unsigned grid = (unsigned)radix_tiles(a.n, R);
+  if (R == 8) {
+    const uint32_t sm = pass_smem<8>();
+    cudaError_t e = cudaFuncSetAttribute(radix_pass_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    radix_pass_kernel<8><<<grid, kThreads, sm, st>>>(a, digit);
+  } else {
+    const uint32_t sm = pass_smem<16>();
+    cudaError_t e = cudaFuncSetAttribute(radix_pass_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    radix_pass_kernel<16><<<grid, kThreads, sm, st>>>(a, digit);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bos

@@ -1,0 +1,234 @@
+"""CUDA path against the oracle, element by element, through the C ABI (libbos.so).
+
+Integer and byte work: every comparison is bit-exact. The oracle's closed form is used for
+speed; it is pinned to the literal Algorithm 3.1 by the CPU tests.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_01765_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bos():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_01765_gb300 import _build
+    _build.build()
+    from paper_2008_01765_gb300 import bos as b
+    b.lib()
+    return b
+
+
+def gpu_orp(bos, recs, Z, seed, **kw):
+    out, info = bos.orp(bos.to_device(recs), recs.dtype.itemsize, Z=Z, seed=seed, **kw)
+    return bos.to_host(out, recs.dtype), info
+
+
+def gpu_sort(bos, recs, Z, seed, **kw):
+    out, info = bos.sort(bos.to_device(recs), recs.dtype.itemsize, Z=Z, seed=seed, **kw)
+    return bos.to_host(out, recs.dtype), info
+
+
+def test_philox_matches_curand_and_oracle(bos):
+    import torch
+    rng = np.random.default_rng(5)
+    n = 1 << 20
+    ctr = rng.integers(0, 1 << 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 1 << 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:1000] = 0  # include the all-zero corner and small counters
+    ctr[:1000, 2] = np.arange(1000)
+    mine, ref = bos.selftest_philox(torch.from_numpy(ctr.view(np.int32)).cuda(),
+                                    torch.from_numpy(key.view(np.int32)).cuda())
+    mine = mine.cpu().numpy().view(np.uint32)
+    ref = ref.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(mine, ref)
+    np.testing.assert_array_equal(mine, oracle.philox_many(ctr, key))
+
+
+ORP_CASES = [
+    # (n, Z, rec_bytes, k)
+    (1, 512, 8, 0), (2, 4, 8, 0), (3, 4, 16, 0), (5, 2, 8, 0), (7, 3, 16, 0),
+    (100, 8, 8, 0), (1000, 32, 16, 0), (4097, 64, 8, 0), (4097, 64, 8, 1),
+    (12345, 12, 16, 0), (30000, 5, 8, 0),
+    (1 << 16, 512, 8, 1), (1 << 16, 512, 8, 0), (1 << 16, 512, 16, 0),
+    ((1 << 20) + 3, 512, 16, 0), (300000, 1024, 16, 0), (300000, 1024, 16, 2),
+    ((1 << 18) - 1, 96, 8, 0), (1 << 19, 4096, 8, 0), (1 << 17, 2, 8, 0),
+]
+
+
+@pytest.mark.parametrize("n,Z,rec_bytes,k", ORP_CASES)
+def test_orp_matches_oracle(bos, n, Z, rec_bytes, k):
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=n + Z)
+    for seed in (1, 0xDEADBEEFCAFEF00D):
+        try:
+            ref, rinfo = oracle.orp(recs, Z, seed, max_attempts=64, method=oracle.CLOSED)
+        except oracle.OracleError as e:
+            # tiny Z: every attempt overflows (Lemma 3.2); the library must say so too
+            assert e.status == oracle.ERR_OVERFLOW
+            with pytest.raises(bos.BosError) as ge:
+                gpu_orp(bos, recs, Z, seed, k=k, max_attempts=64)
+            assert ge.value.status == bos.ERR_OVERFLOW
+            continue
+        got, info = gpu_orp(bos, recs, Z, seed, k=k, max_attempts=64)
+        assert info.attempts == rinfo.attempts
+        assert info.B == rinfo.B and info.L == rinfo.L
+        np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rec_bytes", [8, 16])
+@pytest.mark.parametrize("dist", inputs.DISTRIBUTIONS)
+def test_sort_matches_oracle(bos, rec_bytes, dist):
+    for n, Z in [(5000, 64), (1 << 16, 512), (200003, 256)]:
+        recs = inputs.make_records(n, rec_bytes, dist, seed=3)
+        ref, rinfo = oracle.sort(recs, Z, 7, method=oracle.CLOSED)
+        got, info = gpu_sort(bos, recs, Z, 7)
+        assert info.attempts == rinfo.attempts
+        np.testing.assert_array_equal(got, ref)
+        if dist == "equal":
+            assert info.radix_passes == 0
+
+
+def test_result_independent_of_k(bos):
+    recs = inputs.make_records(1 << 18, 16, "dup1024", seed=9)
+    outs = []
+    for k in (1, 2, 3, 4, 0):
+        got, info = gpu_sort(bos, recs, 256, 11, k=k)
+        outs.append(got)
+        if k == 1:
+            assert info.passes == info.L
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
+def test_forced_overflow_retry(bos):
+    recs = inputs.make_records(50000, 16, "uniform", seed=2)
+    got, info = gpu_orp(bos, recs, 128, 5, flags=bos.FLAG_FORCE_OVERFLOW(2))
+    assert info.attempts == 3
+    ref, _ = oracle.orp(recs, 128, 5, method=oracle.CLOSED, first_attempt=2)
+    np.testing.assert_array_equal(got, ref)
+    with pytest.raises(bos.BosError) as e:
+        gpu_orp(bos, recs, 128, 5, flags=bos.FLAG_FORCE_OVERFLOW(3), max_attempts=3)
+    assert e.value.status == bos.ERR_OVERFLOW
+
+
+def test_real_overflow_retries_match_oracle(bos):
+    # n = 4096, Z = 32 (B = 256) overflows in about 14% of attempts (Lemma 3.2); the attempt
+    # that first succeeds must agree with the oracle's.
+    recs = inputs.make_records(4096, 8, "uniform", seed=4)
+    seen_retry = False
+    for seed in range(60):
+        try:
+            ref, rinfo = oracle.orp(recs, 32, seed, max_attempts=16, method=oracle.CLOSED)
+        except oracle.OracleError:
+            with pytest.raises(bos.BosError):
+                gpu_orp(bos, recs, 32, seed, max_attempts=16)
+            continue
+        got, info = gpu_orp(bos, recs, 32, seed, max_attempts=16)
+        assert info.attempts == rinfo.attempts
+        seen_retry |= info.attempts > 1
+        np.testing.assert_array_equal(got, ref)
+    assert seen_retry
+
+
+def test_lookback_timeout_reports_status_and_context_survives(bos):
+    recs = inputs.make_records(20000, 8, "uniform", seed=6)
+    with pytest.raises(bos.BosError) as e:
+        gpu_orp(bos, recs, 64, 3, flags=bos.FLAG_SKIP_PUBLISH)
+    assert e.value.status == bos.ERR_TIMEOUT
+    got, _ = gpu_orp(bos, recs, 64, 3)
+    ref, _ = oracle.orp(recs, 64, 3, method=oracle.CLOSED)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rec_bytes", [8, 16])
+@pytest.mark.parametrize("n", [1, 2, 64, 4096, 1 << 16, 1 << 20])
+def test_bitonic_matches_sort_by_key_payload(bos, rec_bytes, n):
+    recs = inputs.make_records(n, rec_bytes, "dup1024", seed=n, payload="random")
+    out = bos.bitonic_sort(bos.to_device(recs), rec_bytes)
+    got = bos.to_host(out, recs.dtype)
+    np.testing.assert_array_equal(got, np.sort(recs, order=["key", "payload"]))
+
+
+def test_batched_equals_alone(bos):
+    sizes = inputs.batched_sizes(24, 4, 16, seed=3)
+    sizes[0] = 0
+    sizes[1] = 1
+    recs, offs = inputs.make_batch(sizes, 8, seed=2)
+    seeds = np.arange(100, 100 + sizes.size, dtype=np.uint64)
+    ops = (np.arange(sizes.size) % 2).astype(np.uint8)
+    Zs = np.where(np.arange(sizes.size) % 3 == 0, 64, 512).astype(np.uint32)
+    x = bos.to_device(recs)
+    import torch
+    out = torch.empty_like(x)
+    att = bos.sort_batched(x, out, offs, seeds, ops, bos.params(8, 512, 0), Zs=Zs)
+    got = bos.to_host(out, recs.dtype)
+    for j in range(sizes.size):
+        a, b = int(offs[j]), int(offs[j + 1])
+        f = oracle.sort if ops[j] else oracle.orp
+        ref, rinfo = f(recs[a:b], int(Zs[j]), int(seeds[j]), method=oracle.CLOSED)
+        assert att[j] == (rinfo.attempts if b > a else 0)
+        np.testing.assert_array_equal(got[a:b], ref)
+
+
+def _trace(bos, recs, Z, seed, k=0):
+    import torch
+    buf = torch.zeros(1 << 27, dtype=torch.uint8, device="cuda")
+    bos.trace_attach(buf)
+    try:
+        gpu_orp(bos, recs, Z, seed, k=k)
+        torch.cuda.synchronize()
+    finally:
+        bos.trace_attach(None)
+    w = buf.view(torch.int64).cpu().numpy().view(np.uint64)
+    cnt = int(w[0])
+    assert 0 < cnt <= (buf.numel() // 16 - 1)
+    ent = w[2:2 + 2 * cnt].reshape(cnt, 2)
+    order = np.lexsort((ent[:, 1], ent[:, 0]))
+    return ent[order]
+
+
+@pytest.mark.parametrize("k", [1, 0])
+def test_address_trace_is_input_independent(bos, k):
+    n, Z = 1 << 14, 256
+    base = None
+    for dist in ("uniform", "equal", "sorted", "reverse"):
+        recs = inputs.make_records(n, 16, dist, seed=12)
+        t = _trace(bos, recs, Z, seed=4, k=k)
+        if base is None:
+            base = t
+        else:
+            np.testing.assert_array_equal(t, base)
+    # Across seeds the butterfly passes (everything but the compacted output writes, whose
+    # addresses follow the final loads, Lemma 3.3) are identical too.
+    t2 = _trace(bos, inputs.make_records(n, 16, "uniform", seed=12), Z, seed=99, k=k)
+    kind_buf = lambda t: ((t[:, 0] >> np.uint64(48)) & np.uint64(0xFF))
+    keep = lambda t: t[kind_buf(t) != 5]
+    np.testing.assert_array_equal(keep(t2), keep(base))
+    # every slot of every bucket is read and written by each butterfly pass: counts check
+    assert len(keep(base)) > 0
+
+
+def test_cfg1_plain_form_full_size(bos):
+    # n = 2^16 8-byte records, uniform u32 keys, payload = index, Z = 512 (B = 256), seed 1,
+    # one level per launch.
+    recs = inputs.make_records(1 << 16, 8, "uniform", seed=1)
+    ref, rinfo = oracle.sort(recs, 512, 1, method=oracle.CLOSED)
+    got, info = gpu_sort(bos, recs, 512, 1, k=1)
+    assert (info.B, info.L, info.passes) == (256, 8, 8)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "dup1024", "sorted"])
+def test_cfg2_full_size(bos, dist):
+    # n = 2^24 16-byte records, Z = 512 (B = 2^16), fused k-level passes.
+    recs = inputs.make_records(1 << 24, 16, dist, seed=2)
+    ref, rinfo = oracle.sort(recs, 512, 2, method=oracle.CLOSED)
+    got, info = gpu_sort(bos, recs, 512, 2)
+    assert (info.B, info.L) == (1 << 16, 16)
+    assert info.passes < info.L
+    np.testing.assert_array_equal(got, ref)
