@@ -87,6 +87,29 @@ size_t bos_workspace_bytes(uint64_t n, const bos_params* p);
 bos_status bos_orp(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,
                    size_t ws_bytes, void* stream, bos_info* info);
 
+/* Bucket ORP for callers that cannot allocate device memory (the paper has no counterpart; this
+ * is a deployment aid). Callers such as code running inside a device allocator's callbacks, code
+ * running during a relaxed or global-mode stream capture, real-time loops that may not risk an
+ * allocation's implicit synchronisation, or plugins whose host owns all device memory cannot
+ * provide the workspace bos_orp needs. bos_orp_noalloc gives the same result as bos_orp for the
+ * same arguments but takes its workspace from a scratch array compiled into the library:
+ *   - size: BOS_NOALLOC_SCRATCH_BYTES (64 MiB) of device memory, held on every GPU where the
+ *     library's kernels are loaded until the process exits. n is accepted while the ORP's
+ *     workspace for n fits; otherwise the call returns BOS_ERR_WORKSPACE and touches nothing.
+ *     (bos_workspace_bytes(n, p) <= BOS_NOALLOC_SCRATCH_BYTES is a sufficient check; with
+ *     Z = 512 every n <= 2^19 fits for 16-byte records and every n <= 2^20 for 8-byte records.)
+ *   - no allocation: the call makes no cudaMalloc / cudaFree or other allocating call. Its first
+ *     call on a device looks up the scratch's device address (cudaGetSymbolAddress, with that
+ *     device current); make that first call before any stream capture on the device.
+ *   - sharing: every call on a device uses the same scratch, which keeps the previous call's
+ *     contents (the call clears what must start at zero itself). Calls whose GPU work overlaps
+ *     (different streams, or host threads) race on the scratch and give wrong results: order
+ *     them on one stream or serialise them.
+ * Arguments as for bos_orp. */
+#define BOS_NOALLOC_SCRATCH_BYTES (64u << 20)
+bos_status bos_orp_noalloc(const void* d_in, void* d_out, uint64_t n, const bos_params* p,
+                           void* stream, bos_info* info);
+
 /* Bucket oblivious sort (Section 3.3): the ORP of d_in followed by a stable ascending LSD radix
  * sort on the key, so equal keys keep their ORP order. Same arguments as bos_orp. */
 bos_status bos_sort(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,

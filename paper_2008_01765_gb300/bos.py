@@ -76,6 +76,9 @@ def lib():
         L.bos_version.restype = _u32
         L.bos_selftest_philox.argtypes = [_vp, _vp, _vp, _vp, _u64, _vp]
         L.bos_selftest_philox.restype = ctypes.c_int
+        L.bos_orp_noalloc.argtypes = [_vp, _vp, _u64, ctypes.POINTER(Params), _vp,
+                                      ctypes.POINTER(Info)]
+        L.bos_orp_noalloc.restype = ctypes.c_int
         L.bos_profile_enable.argtypes = [ctypes.c_int]
         L.bos_profile_enable.restype = ctypes.c_int
         L.bos_profile_read.argtypes = [ctypes.POINTER(KernelStat), _u32, ctypes.POINTER(_u64)]
@@ -148,6 +151,24 @@ def orp(x, rec_bytes, Z=512, seed=1, k=0, max_attempts=0, flags=0, out=None, wor
     """Bucket ORP of a contiguous CUDA tensor holding n records of rec_bytes bytes each."""
     n = x.numel() * x.element_size() // rec_bytes
     return _run(orp_raw, x, out, n, rec_bytes, Z, seed, k, max_attempts, flags, workspace, stream)
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def orp_noalloc(x, rec_bytes, Z=512, seed=1, k=0, max_attempts=0, flags=0, out=None, stream=None):
+    """bos_orp_noalloc: the bucket ORP without a caller workspace (the library's fixed scratch
+    is used; calls on one device must not overlap). Returns (out, Info)."""
+    import torch
+    n = x.numel() * x.element_size() // rec_bytes
+    if out is None:
+        out = torch.empty_like(x)
+    p = params(rec_bytes, Z, seed, k, max_attempts, flags)
+    info = Info()
+    st = lib().bos_orp_noalloc(_vp(x.data_ptr()), _vp(out.data_ptr()), n, ctypes.byref(p),
+                               _stream_handle(stream), ctypes.byref(info))
+    _check(st, "bos_orp_noalloc")
+    return out, info
 
 
 def sort(x, rec_bytes, Z=512, seed=1, k=0, max_attempts=0, flags=0, out=None, workspace=None,

@@ -290,6 +290,18 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
 }
 
 }  // namespace
+
+size_t orp_workspace_bytes(uint64_t n, const bos_params* p) {
+  Plan pl;
+  if (make_plan(n, p, false, &pl) != BOS_OK) return 0;
+  return n ? pl.total : 0;
+}
+
+bos_status orp_with_workspace(const void* d_in, void* d_out, uint64_t n, const bos_params* p,
+                              void* d_ws, size_t ws_bytes, void* stream, bos_info* info) {
+  return run(d_in, d_out, n, p, d_ws, ws_bytes, stream, info, false);
+}
+
 }  // namespace bos
 
 using namespace bos;

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "bos.h"
 #include "common.cuh"
 
 namespace bos {
@@ -50,6 +51,11 @@ uint64_t radix_tiles(uint64_t n, int R);
 cudaError_t launch_radix_hist(const RadixArgs& a, int R, cudaStream_t st);
 cudaError_t launch_radix_prep(const RadixArgs& a, int R, cudaStream_t st);
 cudaError_t launch_radix_pass(const RadixArgs& a, int R, uint32_t digit, cudaStream_t st);
+
+// Bucket ORP with a caller-chosen workspace (api.cu); workspace bytes of the ORP alone.
+size_t orp_workspace_bytes(uint64_t n, const bos_params* p);
+bos_status orp_with_workspace(const void* d_in, void* d_out, uint64_t n, const bos_params* p,
+                              void* d_ws, size_t ws_bytes, void* stream, bos_info* info);
 
 // Bitonic comparator (bitonic.cu)
 cudaError_t launch_bitonic(const void* in, void* out, uint64_t n, int R, cudaStream_t st);
