@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-form and bitonic comparators")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=22)
+    ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="bos_params.flags (comparisons)")
+    ap.add_argument("--k", type=int, default=0, help="levels per ORP pass (0 = automatic)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     return ap.parse_args()
 
 
@@ -218,13 +221,13 @@ def main():
     x = host_in.to(dev)
     del recs
     out = torch.empty_like(x)
-    p = bos.params(REC, Z, seed=1)
+    p = bos.params(REC, Z, seed=1, flags=args.flags)
     ws = bos.alloc_workspace(bos.workspace_bytes(n, p), dev)
     sh = bos._stream_handle(stream)
 
-    def step(seed, k=0):
+    def step(seed, k=None):
         p.seed = seed
-        p.k = k
+        p.k = args.k if k is None else k
         return bos.sort_raw(x.data_ptr(), out.data_ptr(), n, p, ws.data_ptr(), ws.numel(), sh)
 
     for w in range(args.warmup):
@@ -268,6 +271,7 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": workload, "n": n, "rec_bytes": REC, "Z": Z, "B": int(info.B),
                        "L": int(info.L), "orp_passes": int(info.passes), "radix_passes": int(info.radix_passes),
+                       "max_cluster": int(info.max_cluster), "max_k": int(info.max_k), "flags": args.flags,
                        "keys": f"{args.dist} u64, payload = index", "l2": "inputs (16 GiB) larger than L2",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs": step_bytes / (ms / 1e3) / 1e9, "hbm_frac": step_bytes / (ms / 1e3) / 1e9 / hbm,
@@ -325,7 +329,7 @@ def main():
         line["speedup_vs_plain"] = pms / ms
         line["speedup_vs_bitonic"] = bms / ms
 
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sample_log2, Z, args.dist)
         except Exception as e:  # pragma: no cover

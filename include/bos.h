@@ -55,6 +55,16 @@ typedef enum {
 /* Debug: one look-back producer skips its publish, so the bounded wait must time out and the
  * call must return BOS_ERR_TIMEOUT (tests the failure path without hanging a GPU). */
 #define BOS_FLAG_SKIP_PUBLISH 0x1u
+/* Use the one-CTA-per-subproblem pass kernel even when Z is a multiple of 32 (comparison and
+ * tests; the result is the same). */
+#define BOS_FLAG_GENERIC 0x2u
+/* Do not use thread-block clusters (C = 1): fewer levels per pass, same result. */
+#define BOS_FLAG_NO_CLUSTER 0x4u
+/* Plan the fewest passes (largest clusters) instead of the measured-cost plan; same result. */
+#define BOS_FLAG_FEWEST_PASSES 0x8u
+/* Largest thread-block cluster a pass may use (1, 2, 4, 8 or 16; 0 = the library's choice).
+ * Tuning only: the result never depends on it. */
+#define BOS_FLAG_MAX_CLUSTER(c) (((uint32_t)(c) & 0x1Fu) << 16)
 
 typedef struct {
   uint32_t rec_bytes;    /* 8 or 16 */
@@ -74,6 +84,8 @@ typedef struct {
   uint32_t passes;   /* HBM passes of the ORP in the last attempt */
   uint32_t radix_passes; /* LSD radix passes run by the sort (digits where all keys agree are skipped) */
   uint64_t B;        /* number of buckets: smallest power of two with B * Z >= 2n */
+  uint32_t max_cluster; /* largest thread-block cluster used by a pass (1 = no clusters) */
+  uint32_t max_k;    /* most butterfly levels fused into one pass */
 } bos_info;
 
 /* Bytes of device workspace bos_orp / bos_sort need for n records under *p (0 for n = 0).

@@ -14,10 +14,17 @@ LIB_PATH = os.path.join(HERE, "libbos.so")
 
 OK, ERR_INVALID, ERR_OVERFLOW, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(6)
 FLAG_SKIP_PUBLISH = 0x1
+FLAG_GENERIC = 0x2
+FLAG_NO_CLUSTER = 0x4
+FLAG_FEWEST_PASSES = 0x8
 
 
 def FLAG_FORCE_OVERFLOW(n):
     return (n & 0xFF) << 8
+
+
+def FLAG_MAX_CLUSTER(c):
+    return (c & 0x1F) << 16
 
 
 class Params(ctypes.Structure):
@@ -28,7 +35,8 @@ class Params(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("attempts", ctypes.c_uint32), ("L", ctypes.c_uint32), ("passes", ctypes.c_uint32),
-                ("radix_passes", ctypes.c_uint32), ("B", ctypes.c_uint64)]
+                ("radix_passes", ctypes.c_uint32), ("B", ctypes.c_uint64),
+                ("max_cluster", ctypes.c_uint32), ("max_k", ctypes.c_uint32)]
 
 
 class KernelStat(ctypes.Structure):

@@ -1,6 +1,7 @@
 // C ABI of libbos (declared in include/bos.h): argument checks, pass planning, workspace layout
 // and the attempt loop of Algorithm 3.1 (retry with a fresh attempt counter on overflow).
 #include <cstring>
+#include <mutex>
 
 #include "bos.h"
 #include "internal.h"
@@ -70,8 +71,10 @@ struct Plan {
   int R = 16;
   uint32_t key_bytes = 8, Z = 0, L = 0, npass = 0, digits = 8;
   uint64_t n = 0, B = 1;
+  bool fast = false;  // persistent cluster kernel (Z multiple of 32) instead of the generic one
   uint32_t pass_k[kMaxPasses] = {};
   uint32_t pass_i[kMaxPasses] = {};
+  uint32_t pass_C[kMaxPasses] = {};
   // workspace offsets
   size_t off_ctrl = 0, off_rec[2] = {0, 0}, off_tag[2] = {0, 0}, off_status = 0;
   size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, total = 0;
@@ -85,7 +88,34 @@ uint32_t max_k(int R, uint32_t Z, bool last) {
   return best;
 }
 
-bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl) {
+constexpr uint32_t kMaxKFast = 8;
+
+uint32_t max_k_fast(int R, uint32_t Z, uint32_t C, bool last) {
+  uint32_t best = 0;
+  for (uint32_t k = 1; k <= kMaxKFast; ++k)
+    if ((1u << k) >= C && orp_fast_smem_bytes(R, Z, k, C, last) <= kMaxSmem) best = k;
+  return best;
+}
+
+// Splits L levels into passes of at most kmid levels, the last one at most klast; the fewest
+// passes, sizes balanced. Returns the pass count (0 if more than kMaxPasses would be needed).
+uint32_t split_levels(uint32_t L, uint32_t kmid, uint32_t klast, uint32_t* pass_k) {
+  if (kmid == 0 || klast == 0) return 0;
+  for (uint32_t np = 1; np <= kMaxPasses; ++np) {
+    const uint32_t kl = klast < (L + np - 1) / np ? klast : (L + np - 1) / np;
+    const uint32_t rest = L - (kl < L ? kl : L);
+    if (rest <= (np - 1) * kmid) {
+      if (pass_k) {
+        pass_k[np - 1] = L - rest;
+        for (uint32_t x = 0; x + 1 < np; ++x) pass_k[x] = rest / (np - 1) + (x < rest % (np - 1));
+      }
+      return np;
+    }
+  }
+  return 0;
+}
+
+bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint32_t max_C = 16) {
   if (!p) return BOS_ERR_INVALID;
   if (!((p->rec_bytes == 8 && p->key_bytes == 4) || (p->rec_bytes == 16 && p->key_bytes == 8)))
     return BOS_ERR_INVALID;
@@ -105,37 +135,125 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl) {
   if (B * p->Z >= (1ull << 32)) return BOS_ERR_INVALID;  // slot indices are 32-bit inside a pass
   pl->B = B;
   pl->L = L;
-  // Split the L levels into passes: at most kmid levels per pass, klast in the last pass.
-  uint32_t kmid = max_k(pl->R, p->Z, false), klast = max_k(pl->R, p->Z, true);
-  if (p->k) {
-    kmid = kmid < p->k ? kmid : p->k;
-    klast = klast < p->k ? klast : p->k;
+  pl->fast = (p->Z % 32 == 0) && !(p->flags & BOS_FLAG_GENERIC);
+  if (p->flags & BOS_FLAG_NO_CLUSTER) max_C = 1;
+  const uint32_t cap = (p->flags >> 16) & 0x1Fu;
+  if (cap && cap < max_C) max_C = cap;
+  if (pl->fast && L > 0) {  // no cluster size fits this Z: the generic kernel takes it
+    bool any = false;
+    for (uint32_t C = 1; C <= max_C && !any; C <<= 1)
+      any = max_k_fast(pl->R, p->Z, C, false) && max_k_fast(pl->R, p->Z, C, true);
+    if (!any) pl->fast = false;
   }
   if (L == 0) {
-    if (orp_smem_bytes(pl->R, p->Z, 0, true) > kMaxSmem) return BOS_ERR_INVALID;
+    const uint32_t sm = pl->fast ? orp_fast_smem_bytes(pl->R, p->Z, 0, 1, true) : orp_smem_bytes(pl->R, p->Z, 0, true);
+    if (sm > kMaxSmem) return BOS_ERR_INVALID;
     pl->npass = 1;
     pl->pass_k[0] = 0;
-  } else {
-    if (kmid == 0 || klast == 0) return BOS_ERR_INVALID;
-    uint32_t np = 1;
-    while (true) {
-      const uint32_t kl = klast < (L + np - 1) / np ? klast : (L + np - 1) / np;
-      const uint32_t rest = L - (kl < L ? kl : L);
-      if (rest <= (np - 1) * kmid) {
-        pl->pass_k[np - 1] = L - rest;
-        for (uint32_t x = 0; x + 1 < np; ++x) pl->pass_k[x] = rest / (np - 1) + (x < rest % (np - 1));
-        break;
-      }
-      if (++np > kMaxPasses) return BOS_ERR_INVALID;
+    pl->pass_C[0] = 1;
+  } else if (!pl->fast) {
+    // Split the L levels into passes: at most kmid levels per pass, klast in the last pass.
+    uint32_t kmid = max_k(pl->R, p->Z, false), klast = max_k(pl->R, p->Z, true);
+    if (p->k) {
+      kmid = kmid < p->k ? kmid : p->k;
+      klast = klast < p->k ? klast : p->k;
     }
-    pl->npass = np;
+    pl->npass = split_levels(L, kmid, klast, pl->pass_k);
+    if (!pl->npass) return BOS_ERR_INVALID;
+    for (uint32_t x = 0; x < pl->npass; ++x) pl->pass_C[x] = 1;
+  } else if (p->flags & BOS_FLAG_FEWEST_PASSES) {
+    // Fewest passes over the cluster sizes C (ties: the smaller C), then per pass the smallest
+    // C that holds its k levels.
+    uint32_t best_np = 0, best_C = 1;
+    for (uint32_t C = 1; C <= max_C; C <<= 1) {
+      uint32_t kmid = max_k_fast(pl->R, p->Z, C, false), klast = max_k_fast(pl->R, p->Z, C, true);
+      if (p->k) {
+        kmid = kmid < p->k ? kmid : p->k;
+        klast = klast < p->k ? klast : p->k;
+      }
+      const uint32_t np = split_levels(L, kmid, klast, nullptr);
+      if (np && (!best_np || np < best_np)) {
+        best_np = np;
+        best_C = C;
+      }
+    }
+    if (!best_np) return BOS_ERR_INVALID;
+    uint32_t kmid = max_k_fast(pl->R, p->Z, best_C, false), klast = max_k_fast(pl->R, p->Z, best_C, true);
+    if (p->k) {
+      kmid = kmid < p->k ? kmid : p->k;
+      klast = klast < p->k ? klast : p->k;
+    }
+    pl->npass = split_levels(L, kmid, klast, pl->pass_k);
+    for (uint32_t x = 0; x < pl->npass; ++x) {
+      const bool last = x + 1 == pl->npass;
+      uint32_t C = 1;
+      while (C < best_C && (pl->pass_k[x] > max_k_fast(pl->R, p->Z, C, last) || (1u << pl->pass_k[x]) < C)) C <<= 1;
+      pl->pass_C[x] = C;
+    }
+  } else {
+    // Cost model from GB300 measurements of the persistent kernel (time per slot of a butterfly
+    // pass relative to the cluster-free kernel): a cluster applies more levels per pass but its
+    // two cluster barriers per subproblem slow each pass. The first and the last pass (which
+    // also draw labels or build the in-bin permutations) run without clusters; the middle levels
+    // take the cluster size with the lowest total cost. Ties go to fewer passes.
+    static const double kRel[5] = {1.0, 1.09, 1.37, 1.63, 2.46};  // C = 1, 2, 4, 8, 16
+    uint32_t kf = max_k_fast(pl->R, p->Z, 1, false), kl = max_k_fast(pl->R, p->Z, 1, true);
+    uint32_t ks = kl;  // single FIRST+LAST pass
+    if (p->k) {
+      kf = kf < p->k ? kf : p->k;
+      kl = kl < p->k ? kl : p->k;
+      ks = ks < p->k ? ks : p->k;
+    }
+    if (kf == 0 || kl == 0) return BOS_ERR_INVALID;  // (checked above)
+    if (L <= ks) {
+      pl->npass = 1;
+      pl->pass_k[0] = L;
+      pl->pass_C[0] = 1;
+    } else {
+      double best = 1e30;
+      uint32_t best_f = 0, best_l = 0, best_C = 1, best_m = 0;
+      for (uint32_t f = 1; f <= kf && f < L; ++f) {
+        for (uint32_t l = 1; l <= kl && f + l <= L; ++l) {
+          const uint32_t M = L - f - l;
+          for (uint32_t ci = 0, C = 1; C <= max_C; ++ci, C <<= 1) {
+            uint32_t km = max_k_fast(pl->R, p->Z, C, false);
+            if (p->k) km = km < p->k ? km : p->k;
+            if (M > 0 && km == 0) continue;
+            const uint32_t m = M ? (M + km - 1) / km : 0;
+            const double cost = 2.0 + m * (M ? kRel[ci] : 0.0) - 1e-3 * (f + l);
+            if (cost < best - 1e-9) {
+              best = cost;
+              best_f = f;
+              best_l = l;
+              best_C = C;
+              best_m = m;
+            }
+            if (!M) break;
+          }
+        }
+      }
+      if (best_f == 0 || 2 + best_m > kMaxPasses) return BOS_ERR_INVALID;
+      const uint32_t M = L - best_f - best_l;
+      pl->npass = 2 + best_m;
+      pl->pass_k[0] = best_f;
+      pl->pass_C[0] = 1;
+      for (uint32_t x = 0; x < best_m; ++x) {
+        pl->pass_k[1 + x] = M / best_m + (x < M % best_m);
+        uint32_t C = 1;  // smallest cluster that holds this pass's levels
+        while (C < best_C && (pl->pass_k[1 + x] > max_k_fast(pl->R, p->Z, C, false) || (1u << pl->pass_k[1 + x]) < C))
+          C <<= 1;
+        pl->pass_C[1 + x] = C;
+      }
+      pl->pass_k[pl->npass - 1] = best_l;
+      pl->pass_C[pl->npass - 1] = 1;
+    }
   }
   uint32_t lvl = 0;
   for (uint32_t x = 0; x < pl->npass; ++x) {
     pl->pass_i[x] = lvl;
     lvl += pl->pass_k[x];
   }
-  // workspace
+  // workspace (independent of k and of the kernel choice)
   const uint64_t slots = B * p->Z;
   size_t off = 0;
   pl->off_ctrl = off; off = align256(off + sizeof(Ctrl));
@@ -159,6 +277,49 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl) {
   return BOS_OK;
 }
 
+// Occupancy of a fast-kernel configuration on the current device (cached per configuration).
+int fast_occupancy_cached(int R, int mode, uint32_t Z, uint32_t k, uint32_t C) {
+  struct Entry { int dev, R, mode; uint32_t Z, k, C; int occ; };
+  static std::mutex mu;
+  static Entry cache[256];
+  static int used = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  {
+    std::lock_guard<std::mutex> g(mu);
+    for (int x = 0; x < used; ++x) {
+      const Entry& e = cache[x];
+      if (e.dev == dev && e.R == R && e.mode == mode && e.Z == Z && e.k == k && e.C == C) return e.occ;
+    }
+  }
+  const int occ = orp_fast_occupancy(R, mode, Z, k, C);
+  std::lock_guard<std::mutex> g(mu);
+  if (used < 256) cache[used++] = Entry{dev, R, mode, Z, k, C, occ};
+  return occ;
+}
+
+// Plan for this device: the largest cluster size whose every pass can be scheduled.
+bos_status device_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl) {
+  for (uint32_t max_C = 16;; max_C >>= 1) {
+    const bos_status s = make_plan(n, p, sort, pl, max_C);
+    if (s != BOS_OK || !pl->fast || n == 0) return s;
+    bool ok = true;
+    for (uint32_t x = 0; x < pl->npass && ok; ++x) {
+      const int mode = (x == 0 ? kModeFirst : 0) | (x + 1 == pl->npass ? kModeLast : 0);
+      ok = fast_occupancy_cached(pl->R, mode, pl->Z, pl->pass_k[x], pl->pass_C[x]) > 0;
+    }
+    if (ok) return BOS_OK;
+    if (max_C == 1) {  // the fast kernel cannot run here: use the generic one
+      bos_params q = *p;
+      q.flags |= BOS_FLAG_GENERIC;
+      return make_plan(n, &q, sort, pl, 1);
+    }
+  }
+}
+
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
   return na && nb && x < y + nb && y < x + na;
@@ -175,7 +336,7 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,
                size_t ws_bytes, void* stream, bos_info* info, bool sort) {
   Plan pl;
-  bos_status s = make_plan(n, p, sort, &pl);
+  bos_status s = n ? device_plan(n, p, sort, &pl) : make_plan(n, p, sort, &pl);
   if (s != BOS_OK) return s;
   if (info) {
     info->attempts = 0;
@@ -183,6 +344,12 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     info->passes = pl.npass;
     info->radix_passes = 0;
     info->B = pl.B;
+    info->max_cluster = 1;
+    info->max_k = 0;
+    for (uint32_t x = 0; x < pl.npass; ++x) {
+      info->max_cluster = pl.pass_C[x] > info->max_cluster ? pl.pass_C[x] : info->max_cluster;
+      info->max_k = pl.pass_k[x] > info->max_k ? pl.pass_k[x] : info->max_k;
+    }
   }
   if (n == 0) return BOS_OK;
   const size_t bytes = n * pl.R;
@@ -265,7 +432,10 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       const double out_b = last ? (double)n * pl.R : slot_bytes;
       const int cls = first && last ? kKSingle : first ? kKFirst : last ? kKLast : kKMid;
       const int ev = prof_begin(st, cls, in_b + out_b);
-      BOS_CUDA(launch_orp_pass(a, mode, pl.B >> a.k, st, pl.R, trace));
+      if (pl.fast)
+        BOS_CUDA(launch_orp_fast(a, mode, pl.pass_C[x], 0, st, pl.R, trace));
+      else
+        BOS_CUDA(launch_orp_pass(a, mode, pl.B >> a.k, st, pl.R, trace));
       prof_end(ev, st);
     }
     if (sort)

@@ -99,13 +99,15 @@ static_assert(sizeof(Ctrl) == 256, "control block size");
 // Bounded spin: number of polls before a wait gives up (~0.5 s with the back-off below).
 constexpr uint32_t kSpinLimit = 1u << 22;
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+// Look-back status words carry their own value (state, tag and count in one 64-bit word) and
+// no other data depends on them, so relaxed device-scope accesses suffice (no fences).
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Look-back status word: bits 62..63 = state (1 aggregate, 2 inclusive prefix), bits 56..61 =
@@ -130,7 +132,7 @@ __device__ __forceinline__ unsigned long long lookback(const unsigned long long*
     unsigned long long w = 0;
     uint32_t spins = 0;
     while (true) {
-      w = ld_acquire_u64(status + (uint64_t)j * stride);
+      w = ld_status(status + (uint64_t)j * stride);
       if ((w >> 62) != 0 && ((w >> 56) & 63u) == tag) break;
       if (++spins > kSpinLimit) {
         atomicExch(&ctrl->timeout, 1u);
@@ -144,6 +146,82 @@ __device__ __forceinline__ unsigned long long lookback(const unsigned long long*
   }
   return prefix;
 }
+
+// Windowed variant: each step issues the loads of W predecessors at once (independent loads, one
+// round-trip per W tiles), then folds them in order, waiting (bounded) on any not yet published.
+template <int W>
+__device__ __forceinline__ unsigned long long lookback_window(const unsigned long long* status, uint64_t tile,
+                                                              uint64_t stride, uint32_t tag, Ctrl* ctrl) {
+  unsigned long long prefix = 0;
+  int64_t j = (int64_t)tile - 1;
+  while (j >= 0) {
+    unsigned long long w[W];
+#pragma unroll
+    for (int x = 0; x < W; ++x) w[x] = (j - x >= 0) ? ld_status(status + (uint64_t)(j - x) * stride) : 0ull;
+#pragma unroll
+    for (int x = 0; x < W; ++x) {
+      if (j - x < 0) return prefix;
+      unsigned long long v = w[x];
+      uint32_t spins = 0;
+      while (!((v >> 62) != 0 && ((v >> 56) & 63u) == tag)) {
+        if (++spins > kSpinLimit) {
+          atomicExch(&ctrl->timeout, 1u);
+          return prefix;
+        }
+        if (spins > 16) __nanosleep(32);
+        v = ld_status(status + (uint64_t)(j - x) * stride);
+      }
+      prefix += v & kStValue;
+      if (v & kStIncl) return prefix;
+    }
+    j -= W;
+  }
+  return prefix;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Shared-memory addresses, mbarriers and TMA bulk copies (cp.async.bulk)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// ---- mbarrier + TMA bulk copies ----
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait on an mbarrier phase; false (and ctrl->timeout) if it never completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, Ctrl* ctrl) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  atomicExch(&ctrl->timeout, 1u);
+  return false;
+}
+__device__ __forceinline__ void tma_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------------------------
 // Debug address trace: {(kind << 56) | (buffer << 48) | bytes, byte offset}.

@@ -35,6 +35,13 @@ uint32_t orp_smem_bytes(int R, uint32_t Z, uint32_t k, bool last);
 cudaError_t launch_orp_pass(const PassArgs& a, int mode, uint64_t grid, cudaStream_t st, int R,
                             bool trace);
 
+// Persistent, cluster-wide ORP pass (orp_fast.cu); Z must be a multiple of 32.
+uint32_t orp_fast_smem_bytes(int R, uint32_t Z, uint32_t k, uint32_t C, bool last);
+// Co-resident clusters (C > 1) or CTAs per SM (C = 1) of that configuration; 0 = cannot run.
+int orp_fast_occupancy(int R, int mode, uint32_t Z, uint32_t k, uint32_t C);
+cudaError_t launch_orp_fast(const PassArgs& a, int mode, uint32_t C, uint32_t max_clusters, cudaStream_t st,
+                            int R, bool trace);
+
 // LSD radix sort (radix.cu)
 struct RadixArgs {
   const void* in;                 // histogram source (any order of the same multiset)

@@ -302,11 +302,11 @@ __global__ void __launch_bounds__(kThreads, 1) orp_pass_kernel(PassArgs a) {
       unsigned long long prefix = 0;
       const bool skip = a.skip_publish && q == 0;
       if (q == 0) {
-        if (!skip) st_release_u64(a.status, st_word(kStIncl, 0, total));
+        if (!skip) st_status(a.status, st_word(kStIncl, 0, total));
       } else {
-        st_release_u64(a.status + q, st_word(kStAgg, 0, total));
-        prefix = lookback(a.status, q, 1, 0, a.ctrl);
-        st_release_u64(a.status + q, st_word(kStIncl, 0, prefix + total));
+        st_status(a.status + q, st_word(kStAgg, 0, total));
+        prefix = lookback_window<8>(a.status, q, 1, 0, a.ctrl);
+        st_status(a.status + q, st_word(kStIncl, 0, prefix + total));
       }
       misc[1] = (uint32_t)prefix;
       misc[2] = (uint32_t)(prefix >> 32);

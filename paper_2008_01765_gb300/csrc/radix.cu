@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) radix_prep_kernel(RadixArgs a) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads) radix_pass_kernel(RadixArgs a, uint32_t digit) {
+__global__ void __launch_bounds__(kThreads, 2) radix_pass_kernel(RadixArgs a, uint32_t digit) {
   using Rec = typename RecT<R>::T;
   const uint32_t live = a.ctrl->radix_live;
   if (!((live >> digit) & 1u)) return;
@@ -93,27 +93,32 @@ __global__ void __launch_bounds__(kThreads) radix_pass_kernel(RadixArgs a, uint3
   const uint32_t lt_mask = lanemask_lt();
 
   Rec rc[kItems];
-  uint32_t dg[kItems], rk[kItems];
+  uint32_t dr[kItems];  // digit (bits 0..8, 256 = none) | rank inside the warp << 9
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const uint64_t idx = t0 + warp * 32 * kItems + it * 32 + lane;
-    dg[it] = 256;
+    dr[it] = 256;
     if (idx < a.n) {
       rc[it] = src[idx];
-      dg[it] = (uint32_t)(RecT<R>::key(rc[it]) >> shift) & 255u;
+      dr[it] = (uint32_t)(RecT<R>::key(rc[it]) >> shift) & 255u;
     }
   }
+  // stable rank inside the warp: positions are warp-contiguous, lane-striped per item
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg[it]);
+    const uint32_t d = dr[it];
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
     const uint32_t lt = __popc(peers & lt_mask);
-    rk[it] = wcnt[warp * 257 + dg[it]] + lt;
+    const uint32_t r = wcnt[warp * 257 + d] + lt;
     __syncwarp();
-    if (lt == 0) wcnt[warp * 257 + dg[it]] += __popc(peers);
+    if (lt == 0) wcnt[warp * 257 + d] += __popc(peers);
     __syncwarp();
+    dr[it] = d | (r << 9);
   }
   __syncthreads();
-  // per digit value: tile count, exclusive offsets over warps
+  // per digit value: tile count (published at once), exclusive offsets over warps
+  const uint32_t tag = digit + 1;
+  unsigned long long* st = a.status + tile * 256 + tid;
   uint32_t cnt = 0;
   if (tid < 256) {
     for (int w = 0; w < kWarps; ++w) {
@@ -121,21 +126,15 @@ __global__ void __launch_bounds__(kThreads) radix_pass_kernel(RadixArgs a, uint3
       wcnt[w * 257 + tid] = cnt;
       cnt += x;
     }
-    unsigned long long* st = a.status + tile * 256 + tid;
-    const uint32_t tag = digit + 1;
     if (tile == 0) {
-      st_release_u64(st, st_word(kStIncl, tag, cnt));
-      gstart[tid] = a.dbase[digit * 256 + tid];
+      st_status(st, st_word(kStIncl, tag, cnt));
     } else {
-      st_release_u64(st, st_word(kStAgg, tag, cnt));
-      const unsigned long long pre = lookback(a.status + tid, tile, 256, tag, a.ctrl);
-      st_release_u64(st, st_word(kStIncl, tag, pre + cnt));
-      gstart[tid] = a.dbase[digit * 256 + tid] + pre;
+      st_status(st, st_word(kStAgg, tag, cnt));
     }
     lstart[tid] = cnt;
   }
   __syncthreads();
-  // exclusive scan of the 256 tile counts (warp 0..7 hold them; simple serial-in-warp scan)
+  // exclusive scan of the 256 tile counts (warp 0, eight per lane)
   if (warp == 0) {
     uint32_t v[8], sum = 0;
 #pragma unroll
@@ -158,9 +157,20 @@ __global__ void __launch_bounds__(kThreads) radix_pass_kernel(RadixArgs a, uint3
     if (lane == 31) lstart[256] = run;
   }
   __syncthreads();
+  // stage the tile in digit order (independent of the global prefix)
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
-    if (dg[it] < 256) stage[lstart[dg[it]] + wcnt[warp * 257 + dg[it]] + rk[it]] = rc[it];
+    const uint32_t d = dr[it] & 511u;
+    if (d < 256) stage[lstart[d] + wcnt[warp * 257 + d] + (dr[it] >> 9)] = rc[it];
+  }
+  // global offset of every digit value: decoupled look-back over the tiles in ticket order
+  if (tid < 256) {
+    unsigned long long pre = 0;
+    if (tile > 0) {
+      pre = lookback_window<8>(a.status + tid, tile, 256, tag, a.ctrl);
+      st_status(st, st_word(kStIncl, tag, pre + cnt));
+    }
+    gstart[tid] = a.dbase[digit * 256 + tid] + pre;
   }
   __syncthreads();
   const uint32_t total = lstart[256];
@@ -202,6 +212,7 @@ cudaError_t launch_radix_prep(const RadixArgs& a, int R, cudaStream_t st) {
 
 cudaError_t launch_radix_pass(const RadixArgs& a, int R, uint32_t digit, cudaStream_t st) {
   const unsigned grid = (unsigned)radix_tiles(a.n, R);
+  if (grid == 0) return cudaSuccess;
   if (R == 8) {
     const uint32_t sm = pass_smem<8>();
     cudaError_t e = cudaFuncSetAttribute(radix_pass_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

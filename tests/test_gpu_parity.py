@@ -232,3 +232,51 @@ def test_cfg2_full_size(bos, dist):
     assert (info.B, info.L) == (1 << 16, 16)
     assert info.passes < info.L
     np.testing.assert_array_equal(got, ref)
+
+
+KERNEL_CASES = [
+    # (n, Z, rec_bytes, k): Z a multiple of 32 selects the persistent cluster kernel
+    (1 << 12, 64, 8, 0), ((1 << 16) + 77, 512, 8, 0), (1 << 16, 512, 8, 1), ((1 << 20) - 5, 512, 16, 0),
+    (1 << 22, 1024, 16, 0), (300001, 96, 16, 0), (1 << 18, 32, 16, 0), (1 << 19, 4096, 8, 0),
+    (999, 32, 8, 0), (1 << 21, 256, 8, 3), (1 << 12, 32, 16, 0),
+]
+
+
+@pytest.mark.parametrize("n,Z,rec_bytes,k", KERNEL_CASES)
+def test_cluster_kernel_matches_generic_and_oracle(bos, n, Z, rec_bytes, k):
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=n ^ Z)
+    seed = 0x1234 + n
+    try:
+        ref, rinfo = oracle.orp(recs, Z, seed, max_attempts=16, method=oracle.CLOSED)
+    except oracle.OracleError as e:  # every attempt overflows (small Z): all kernels must say so
+        assert e.status == oracle.ERR_OVERFLOW
+        for flags in (0, bos.FLAG_FEWEST_PASSES, bos.FLAG_NO_CLUSTER, bos.FLAG_GENERIC):
+            with pytest.raises(bos.BosError) as ge:
+                gpu_orp(bos, recs, Z, seed, k=k, flags=flags, max_attempts=16)
+            assert ge.value.status == bos.ERR_OVERFLOW
+        return
+    outs = {}
+    for name, flags in (("auto", 0), ("fewest", bos.FLAG_FEWEST_PASSES), ("no_cluster", bos.FLAG_NO_CLUSTER),
+                        ("generic", bos.FLAG_GENERIC)):
+        got, info = gpu_orp(bos, recs, Z, seed, k=k, flags=flags, max_attempts=16)
+        assert info.attempts == rinfo.attempts, name
+        np.testing.assert_array_equal(got, ref, err_msg=name)
+        outs[name] = info
+    if Z % 32 == 0 and k == 0 and outs["auto"].L >= 8:
+        assert outs["fewest"].max_cluster > 1
+        assert outs["fewest"].passes <= outs["auto"].passes <= outs["no_cluster"].passes
+    assert outs["no_cluster"].max_cluster == 1
+
+
+def test_cfg3_geometry_plans(bos):
+    # n = 2^30 and Z = 1024 give L = 21. The fewest-passes plan uses 16-CTA clusters (7 levels a
+    # pass); the measured-cost plan uses fewer levels per pass. Both give the oracle's result.
+    # Checked on n = 2^22 (L = 13) with the same Z and record width.
+    recs = inputs.make_records(1 << 22, 16, "uniform", seed=3)
+    ref, _ = oracle.sort(recs, 1024, 5, method=oracle.CLOSED)
+    got, info = gpu_sort(bos, recs, 1024, 5, flags=bos.FLAG_FEWEST_PASSES)
+    np.testing.assert_array_equal(got, ref)
+    assert info.max_k == 7 and info.max_cluster == 16 and info.passes == 2
+    got, info = gpu_sort(bos, recs, 1024, 5)
+    np.testing.assert_array_equal(got, ref)
+    assert 2 <= info.passes <= 5
