@@ -18,7 +18,8 @@
  *
  * Conventions for every entry point:
  *   - Every pointer named d_* is a device pointer owned by the caller. The library never
- *     allocates or frees memory, never prints and never aborts; it reports errors by status.
+ *     allocates or frees device memory, never prints and never aborts; it reports errors by
+ *     status (host-side scratch of the batched calls is ordinary heap memory).
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is stream-ordered.
  *     bos_orp / bos_sort / bos_sort_batched synchronise `stream` once per attempt to read the
  *     overflow flag (Algorithm 3.1, MergeSplit aborts on overflow; the call retries with a
@@ -127,18 +128,41 @@ bos_status bos_orp_noalloc(const void* d_in, void* d_out, uint64_t n, const bos_
 bos_status bos_sort(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,
                     size_t ws_bytes, void* stream, bos_info* info);
 
-/* Batched ORP / sort of `num` independent arrays stored back to back (spec batching; the
- * paper has no batched form). Array j occupies records [h_offsets[j], h_offsets[j+1]) of d_in
- * and of d_out, is processed with seed h_seeds[j], Z = h_Z[j] (or base->Z when h_Z is NULL)
- * and op h_ops[j] (0 = ORP, 1 = sort). Its result equals bos_orp / bos_sort of that array alone.
- * h_attempts (nullable, num entries) receives the attempts of each array. Host arrays are read
- * during the call only. */
+/* Batched ORP / sort of `num` independent arrays stored back to back (no counterpart in the
+ * paper; the many-arrays form of the same method). Array j occupies records [h_offsets[j],
+ * h_offsets[j+1]) of d_in and of d_out, is processed with seed h_seeds[j], Z = h_Z[j] (or
+ * base->Z when h_Z is NULL) and op h_ops[j] (0 = ORP, 1 = sort). Its result equals bos_orp /
+ * bos_sort of that array alone with the same seed and Z. h_attempts (nullable, num entries)
+ * receives the attempts of each array (0 for an empty array). Host arrays are read during the
+ * call only. All arrays go through one fixed sequence of launches (a memset, the radix
+ * histograms and offsets, one launch per butterfly pass index and mode, one per radix digit);
+ * arrays that overflowed run again as a smaller batch with the next attempt counter.
+ *
+ * bos_sort_batched = bos_batched_prepare + bos_batched_enqueue + bos_batched_collect:
+ *   - prepare writes the launch descriptors into d_ws (a synchronous copy);
+ *   - enqueue only issues that launch sequence on `stream` (no copy, no synchronisation), so it
+ *     can be captured into a CUDA graph and replayed for the same batch;
+ *   - collect synchronises `stream`, reads every array's overflow flag, reruns the arrays that
+ *     overflowed and writes the full batch's descriptors back (so a captured graph stays valid).
+ * The three calls take the same arguments (d_ws must be the same buffer). */
 size_t bos_batched_workspace_bytes(const uint64_t* h_offsets, uint32_t num, const uint32_t* h_Z,
-                                   const bos_params* base);
+                                   const uint8_t* h_ops, const bos_params* base);
 bos_status bos_sort_batched(const void* d_in, void* d_out, const uint64_t* h_offsets,
                             uint32_t num, const uint64_t* h_seeds, const uint32_t* h_Z,
                             const uint8_t* h_ops, const bos_params* base, void* d_ws,
                             size_t ws_bytes, void* stream, uint32_t* h_attempts);
+bos_status bos_batched_prepare(const void* d_in, void* d_out, const uint64_t* h_offsets,
+                               uint32_t num, const uint64_t* h_seeds, const uint32_t* h_Z,
+                               const uint8_t* h_ops, const bos_params* base, void* d_ws,
+                               size_t ws_bytes, void* stream);
+bos_status bos_batched_enqueue(const void* d_in, void* d_out, const uint64_t* h_offsets,
+                               uint32_t num, const uint64_t* h_seeds, const uint32_t* h_Z,
+                               const uint8_t* h_ops, const bos_params* base, void* d_ws,
+                               size_t ws_bytes, void* stream);
+bos_status bos_batched_collect(const void* d_in, void* d_out, const uint64_t* h_offsets,
+                               uint32_t num, const uint64_t* h_seeds, const uint32_t* h_Z,
+                               const uint8_t* h_ops, const bos_params* base, void* d_ws,
+                               size_t ws_bytes, void* stream, uint32_t* h_attempts);
 
 /* GPU bitonic sorting network (Table 1's comparator; not oblivious-sort output compatible:
  * equal keys are ordered by payload). n must be a power of two (BOS_ERR_INVALID otherwise).

@@ -70,11 +70,18 @@ def lib():
             f.argtypes = [_vp, _vp, _u64, ctypes.POINTER(Params), _vp, ctypes.c_size_t, _vp,
                           ctypes.POINTER(Info)]
             f.restype = ctypes.c_int
-        L.bos_batched_workspace_bytes.argtypes = [_vp, _u32, _vp, ctypes.POINTER(Params)]
+        L.bos_batched_workspace_bytes.argtypes = [_vp, _u32, _vp, _vp, ctypes.POINTER(Params)]
         L.bos_batched_workspace_bytes.restype = ctypes.c_size_t
-        L.bos_sort_batched.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp, ctypes.POINTER(Params),
-                                       _vp, ctypes.c_size_t, _vp, _vp]
-        L.bos_sort_batched.restype = ctypes.c_int
+        for name in ("bos_sort_batched", "bos_batched_collect"):
+            f = getattr(L, name)
+            f.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp, ctypes.POINTER(Params), _vp,
+                          ctypes.c_size_t, _vp, _vp]
+            f.restype = ctypes.c_int
+        for name in ("bos_batched_prepare", "bos_batched_enqueue"):
+            f = getattr(L, name)
+            f.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp, ctypes.POINTER(Params), _vp,
+                          ctypes.c_size_t, _vp]
+            f.restype = ctypes.c_int
         L.bos_bitonic_sort.argtypes = [_vp, _vp, _u64, _u32, _u32, _vp]
         L.bos_bitonic_sort.restype = ctypes.c_int
         L.bos_trace_attach.argtypes = [_vp, ctypes.c_size_t]
@@ -197,32 +204,61 @@ def bitonic_sort(x, rec_bytes, out=None, stream=None):
     return out
 
 
-def batched_workspace_bytes(offsets, Zs, base: Params):
-    off = np.ascontiguousarray(offsets, dtype=np.uint64)
-    z = None if Zs is None else np.ascontiguousarray(Zs, dtype=np.uint32)
-    return int(lib().bos_batched_workspace_bytes(off.ctypes.data_as(_vp), off.size - 1,
-                                                 None if z is None else z.ctypes.data_as(_vp),
-                                                 ctypes.byref(base)))
+class Batch:
+    """A batch of back-to-back arrays (bos_sort_batched and its prepare/enqueue/collect steps).
+
+    x, out: CUDA uint8 tensors holding all records; offsets: num + 1 record offsets; seeds, ops
+    (0 = ORP, 1 = sort) and Zs (optional) per array. The host tables are kept alive here, as the
+    enqueue step may be captured into a CUDA graph.
+    """
+
+    def __init__(self, x, out, offsets, seeds, ops, base: Params, Zs=None, workspace=None):
+        self.x, self.out, self.base = x, out, base
+        self.off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        self.seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        self.ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        self.Zs = None if Zs is None else np.ascontiguousarray(Zs, dtype=np.uint32)
+        self.num = self.off.size - 1
+        need = int(lib().bos_batched_workspace_bytes(
+            self.off.ctypes.data_as(_vp), self.num,
+            None if self.Zs is None else self.Zs.ctypes.data_as(_vp), self.ops.ctypes.data_as(_vp),
+            ctypes.byref(base)))
+        if need == 0 and self.num:
+            raise BosError(ERR_INVALID, "bos_batched_workspace_bytes")
+        if workspace is None or workspace.numel() < need:
+            workspace = alloc_workspace(need, x.device)
+        self.ws = workspace
+        self.attempts = np.zeros(max(self.num, 1), dtype=np.uint32)
+
+    def _args(self):
+        return (_vp(self.x.data_ptr()), _vp(self.out.data_ptr()), self.off.ctypes.data_as(_vp),
+                self.num, self.seeds.ctypes.data_as(_vp),
+                None if self.Zs is None else self.Zs.ctypes.data_as(_vp),
+                self.ops.ctypes.data_as(_vp), ctypes.byref(self.base), _vp(self.ws.data_ptr()),
+                self.ws.numel())
+
+    def run(self, stream=None):
+        st = lib().bos_sort_batched(*self._args(), _stream_handle(stream),
+                                    self.attempts.ctypes.data_as(_vp))
+        _check(st, "bos_sort_batched")
+        return self.attempts[:self.num]
+
+    def prepare(self, stream=None):
+        _check(lib().bos_batched_prepare(*self._args(), _stream_handle(stream)), "bos_batched_prepare")
+
+    def enqueue(self, stream=None):
+        _check(lib().bos_batched_enqueue(*self._args(), _stream_handle(stream)), "bos_batched_enqueue")
+
+    def collect(self, stream=None):
+        st = lib().bos_batched_collect(*self._args(), _stream_handle(stream),
+                                       self.attempts.ctypes.data_as(_vp))
+        _check(st, "bos_batched_collect")
+        return self.attempts[:self.num]
 
 
 def sort_batched(x, out, offsets, seeds, ops, base: Params, Zs=None, workspace=None, stream=None):
     """Batched ORP/sort of back-to-back arrays; returns the attempts per array."""
-    off = np.ascontiguousarray(offsets, dtype=np.uint64)
-    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
-    op = np.ascontiguousarray(ops, dtype=np.uint8)
-    z = None if Zs is None else np.ascontiguousarray(Zs, dtype=np.uint32)
-    num = off.size - 1
-    need = batched_workspace_bytes(off, z, base)
-    if workspace is None or workspace.numel() < need:
-        workspace = alloc_workspace(need, x.device)
-    att = np.zeros(max(num, 1), dtype=np.uint32)
-    st = lib().bos_sort_batched(_vp(x.data_ptr()), _vp(out.data_ptr()), off.ctypes.data_as(_vp),
-                                num, sd.ctypes.data_as(_vp), z.ctypes.data_as(_vp) if z is not None
-                                else None, op.ctypes.data_as(_vp), ctypes.byref(base),
-                                _vp(workspace.data_ptr()), workspace.numel(),
-                                _stream_handle(stream), att.ctypes.data_as(_vp))
-    _check(st, "bos_sort_batched")
-    return att[:num]
+    return Batch(x, out, offsets, seeds, ops, base, Zs, workspace).run(stream)
 
 
 def trace_attach(buf):

@@ -2,6 +2,7 @@
 // and the attempt loop of Algorithm 3.1 (retry with a fresh attempt counter on overflow).
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "bos.h"
 #include "internal.h"
@@ -459,6 +460,314 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   return BOS_ERR_OVERFLOW;
 }
 
+// ============================================================================================
+// Batched ORP / sort: many independent arrays through one fixed sequence of launches (one per
+// butterfly pass index and mode, one per radix stage), suitable for capture into a CUDA graph.
+// Every array uses the one-CTA-per-subproblem pass kernel; its plan, seed and Z are its own, so
+// its result equals bos_orp / bos_sort of that array alone.
+// ============================================================================================
+constexpr uint32_t kBatchMaxPass = 16;
+constexpr size_t kBatchHeader = 1024;  // launch tickets (zeroed with the control blocks)
+
+struct BatchIn {
+  const void* d_in;
+  void* d_out;
+  const uint64_t* off;
+  uint32_t num;
+  const uint64_t* seeds;
+  const uint32_t* Zs;
+  const uint8_t* ops;
+  bos_params base;
+};
+
+struct BatchArr {
+  Plan pl;
+  bool sort = false;
+  size_t zero_off = 0, data_off = 0;  // per-array regions
+  size_t st_off = 0, hist_off = 0, rst_off = 0;                      // inside the zero region
+  size_t rec_off[2] = {0, 0}, tag_off[2] = {0, 0}, tmp_off = 0, dbase_off = 0;  // data region
+};
+
+struct BatchLayout {
+  std::vector<BatchArr> arr;
+  size_t ctrl_off = 0, zero_end = 0, desc_off = 0, desc_bytes = 0, data_off = 0, total = 0;
+  int R = 8;
+  uint32_t maxpass = 0, digits = 4;
+};
+
+bos_status batch_layout(const BatchIn& b, BatchLayout* L) {
+  if (!b.off || (!b.seeds && b.num) || (!b.ops && b.num)) return BOS_ERR_INVALID;
+  L->R = (int)b.base.rec_bytes;
+  L->digits = b.base.key_bytes;
+  L->arr.assign(b.num, BatchArr{});
+  size_t off = 0;
+  off += kBatchHeader;
+  L->ctrl_off = off;
+  off += (size_t)b.num * sizeof(Ctrl);
+  for (uint32_t j = 0; j < b.num; ++j) {
+    if (b.off[j + 1] < b.off[j]) return BOS_ERR_INVALID;
+    BatchArr& a = L->arr[j];
+    bos_params p = b.base;
+    p.flags = (p.flags | BOS_FLAG_GENERIC) & ~BOS_FLAG_SKIP_PUBLISH;
+    if (b.Zs) p.Z = b.Zs[j];
+    a.sort = b.ops[j] != 0;
+    const bos_status s = make_plan(b.off[j + 1] - b.off[j], &p, a.sort, &a.pl);
+    if (s != BOS_OK) return s;
+    if (a.pl.npass > kBatchMaxPass) return BOS_ERR_INVALID;
+    L->maxpass = a.pl.npass > L->maxpass ? a.pl.npass : L->maxpass;
+    a.zero_off = off;
+    a.st_off = off; off = align256(off + a.pl.B * 8);
+    if (a.sort) {
+      a.hist_off = off; off = align256(off + L->digits * 256 * 4);
+      a.rst_off = off;  off = align256(off + radix_tiles(a.pl.n, L->R) * 256 * 8);
+    }
+  }
+  L->zero_end = off;
+  // descriptors: PassArgs for every (array, pass), RadixArgs per array, prefix arrays
+  L->desc_off = off;
+  size_t dsz = 0;
+  for (uint32_t j = 0; j < b.num; ++j) dsz += L->arr[j].pl.npass * sizeof(PassArgs);
+  dsz += (size_t)b.num * sizeof(RadixArgs);
+  dsz += (size_t)(kBatchMaxPass * 4 + 2) * (b.num + 1) * sizeof(uint64_t);
+  L->desc_bytes = align256(dsz);
+  off = align256(off + L->desc_bytes);
+  L->data_off = off;
+  for (uint32_t j = 0; j < b.num; ++j) {
+    BatchArr& a = L->arr[j];
+    const uint64_t slots = a.pl.B * a.pl.Z;
+    const uint32_t arrays = a.pl.L >= 2 ? 2 : a.pl.L;
+    a.data_off = off;
+    for (uint32_t x = 0; x < arrays; ++x) {
+      a.rec_off[x] = off; off = align256(off + slots * L->R);
+      a.tag_off[x] = off; off = align256(off + slots * 4);
+    }
+    if (a.sort) {
+      a.tmp_off = off;   off = align256(off + a.pl.n * L->R);
+      a.dbase_off = off; off = align256(off + L->digits * 256 * 8);
+    }
+  }
+  L->total = off;
+  return BOS_OK;
+}
+
+// One launch of the sequence: an ORP pass (index, mode) or a radix stage.
+struct BatchLaunch {
+  int kind;  // 0 = ORP pass, 1 = radix histogram, 2 = radix offsets, 3 = radix digit pass
+  int mode;
+  uint32_t digit, smem;
+  BatchPass bp;
+  BatchRadix br;
+};
+
+// Builds the launch sequence for the arrays in `sel` (attempt[j] each) and, when `desc` is not
+// null, the descriptor bytes to copy into the workspace's descriptor region.
+bos_status batch_build(const BatchIn& b, const BatchLayout& L, char* ws, const std::vector<uint32_t>& sel,
+                       const std::vector<uint32_t>& attempt, std::vector<BatchLaunch>* launches,
+                       std::vector<char>* desc) {
+  launches->clear();
+  if (desc) desc->assign(L.desc_bytes, 0);
+  size_t dpos = 0;
+  auto dev = [&](size_t pos) { return ws + L.desc_off + pos; };
+  uint32_t ticket_slot = 0;
+  uint32_t* tickets = (uint32_t*)ws;  // header
+  const int R = L.R;
+  // radix descriptors (sort arrays among sel, in sel order)
+  std::vector<uint32_t> sorts;
+  for (uint32_t j : sel)
+    if (L.arr[j].sort && L.arr[j].pl.n) sorts.push_back(j);
+  const size_t ra_pos = dpos;
+  dpos += sorts.size() * sizeof(RadixArgs);
+  const size_t rfirst_pos = dpos;
+  dpos += (sorts.size() + 1) * sizeof(uint64_t);
+  {
+    uint64_t acc = 0;
+    for (size_t x = 0; x < sorts.size(); ++x) {
+      const uint32_t j = sorts[x];
+      const BatchArr& a = L.arr[j];
+      RadixArgs ra{};
+      ra.in = (const char*)b.d_in + b.off[j] * R;
+      ra.buf0 = (char*)b.d_out + b.off[j] * R;
+      ra.buf1 = ws + a.tmp_off;
+      ra.n = a.pl.n;
+      ra.hist = (uint32_t*)(ws + a.hist_off);
+      ra.dbase = (unsigned long long*)(ws + a.dbase_off);
+      ra.status = (unsigned long long*)(ws + a.rst_off);
+      ra.ctrl = (Ctrl*)(ws + L.ctrl_off + (size_t)j * sizeof(Ctrl));
+      ra.ticket_base = 0;
+      if (desc) {
+        std::memcpy(desc->data() + ra_pos + x * sizeof(RadixArgs), &ra, sizeof(ra));
+        std::memcpy(desc->data() + rfirst_pos + x * sizeof(uint64_t), &acc, sizeof(acc));
+      }
+      acc += radix_tiles(a.pl.n, R);
+    }
+    if (desc) std::memcpy(desc->data() + rfirst_pos + sorts.size() * sizeof(uint64_t), &acc, sizeof(acc));
+    BatchRadix br{};
+    br.args = (const RadixArgs*)dev(ra_pos);
+    br.first = (const uint64_t*)dev(rfirst_pos);
+    br.narr = (uint32_t)sorts.size();
+    br.nblocks = acc;
+    br.ticket = tickets + ticket_slot;
+    ticket_slot += L.digits;
+    if (!sorts.empty()) {
+      launches->push_back(BatchLaunch{1, 0, 0, 0, BatchPass{}, br});
+      launches->push_back(BatchLaunch{2, 0, 0, 0, BatchPass{}, br});
+    }
+    // the digit passes come after the ORP passes (pushed at the end)
+    for (uint32_t p = 0; p < L.maxpass; ++p) {
+      for (int mode : {kModeFirst | kModeLast, kModeFirst, 0, kModeLast}) {
+        std::vector<uint32_t> js;
+        for (uint32_t j : sel) {
+          const BatchArr& a = L.arr[j];
+          if (a.pl.n == 0 || p >= a.pl.npass) continue;
+          const int m = (p == 0 ? kModeFirst : 0) | (p + 1 == a.pl.npass ? kModeLast : 0);
+          if (m == mode) js.push_back(j);
+        }
+        if (js.empty()) continue;
+        const size_t args_pos = dpos;
+        dpos += js.size() * sizeof(PassArgs);
+        const size_t first_pos = dpos;
+        dpos += (js.size() + 1) * sizeof(uint64_t);
+        uint64_t acc2 = 0;
+        uint32_t smem = 0;
+        for (size_t x = 0; x < js.size(); ++x) {
+          const uint32_t j = js[x];
+          const BatchArr& a = L.arr[j];
+          PassArgs pa{};
+          const bool first = p == 0, last = p + 1 == a.pl.npass;
+          const uint32_t src = (p + 1) & 1, dst = p & 1;
+          pa.in = (const char*)b.d_in + b.off[j] * R;
+          if (!first) {
+            pa.in_rec = ws + a.rec_off[src];
+            pa.in_tag = (const uint32_t*)(ws + a.tag_off[src]);
+          }
+          if (!last) {
+            pa.out_rec = ws + a.rec_off[dst];
+            pa.out_tag = (uint32_t*)(ws + a.tag_off[dst]);
+          } else {
+            pa.out0 = (char*)b.d_out + b.off[j] * R;
+            pa.out1 = a.sort ? ws + a.tmp_off : pa.out0;
+            pa.out_sel = a.sort ? 1u : 0u;
+            pa.status = (unsigned long long*)(ws + a.st_off);
+          }
+          pa.n = a.pl.n;
+          pa.B = a.pl.B;
+          pa.Z = a.pl.Z;
+          pa.L = a.pl.L;
+          pa.i = a.pl.pass_i[p];
+          pa.k = a.pl.pass_k[p];
+          pa.attempt = attempt[j];
+          pa.seed = b.seeds[j];
+          pa.ctrl = (Ctrl*)(ws + L.ctrl_off + (size_t)j * sizeof(Ctrl));
+          const uint32_t sm = orp_smem_bytes(R, pa.Z, pa.k, last);
+          smem = sm > smem ? sm : smem;
+          if (desc) {
+            std::memcpy(desc->data() + args_pos + x * sizeof(PassArgs), &pa, sizeof(pa));
+            std::memcpy(desc->data() + first_pos + x * sizeof(uint64_t), &acc2, sizeof(acc2));
+          }
+          acc2 += a.pl.B >> pa.k;
+        }
+        if (desc) std::memcpy(desc->data() + first_pos + js.size() * sizeof(uint64_t), &acc2, sizeof(acc2));
+        BatchPass bp{};
+        bp.args = (const PassArgs*)dev(args_pos);
+        bp.first = (const uint64_t*)dev(first_pos);
+        bp.narr = (uint32_t)js.size();
+        bp.nblocks = acc2;
+        bp.ticket = tickets + ticket_slot++;
+        if (ticket_slot * 4 > kBatchHeader) return BOS_ERR_INVALID;
+        launches->push_back(BatchLaunch{0, mode, 0, smem, bp, BatchRadix{}});
+      }
+    }
+    if (!sorts.empty())
+      for (uint32_t d = 0; d < L.digits; ++d) launches->push_back(BatchLaunch{3, 0, d, 0, BatchPass{}, br});
+  }
+  if (dpos > L.desc_bytes) return BOS_ERR_INVALID;
+  return BOS_OK;
+}
+
+bos_status batch_enqueue(const BatchLayout& L, char* ws, const std::vector<BatchLaunch>& launches, cudaStream_t st) {
+  BOS_CUDA(cudaMemsetAsync(ws, 0, L.zero_end, st));
+  for (const BatchLaunch& l : launches) {
+    if (l.kind == 0) {
+      BOS_CUDA(launch_orp_pass_batched(l.bp, l.mode, l.smem, st, L.R));
+    } else {
+      BOS_CUDA(launch_radix_batched(l.br, L.R, l.kind - 1, l.digit, st));
+    }
+  }
+  return BOS_OK;
+}
+
+bos_status batch_check_in(const BatchIn& b, const BatchLayout& L, void* d_ws, size_t ws_bytes) {
+  if (!d_ws || ((uintptr_t)d_ws & 255)) return BOS_ERR_INVALID;
+  if (ws_bytes < L.total) return BOS_ERR_WORKSPACE;
+  const uint64_t nrec = b.num ? b.off[b.num] : 0;
+  if (nrec && (!b.d_in || !b.d_out)) return BOS_ERR_INVALID;
+  if (((uintptr_t)b.d_in % L.R) || ((uintptr_t)b.d_out % L.R)) return BOS_ERR_INVALID;
+  const size_t bytes = nrec * L.R;
+  if (overlaps(b.d_out, bytes, b.d_in, bytes) || overlaps(b.d_out, bytes, d_ws, ws_bytes)) return BOS_ERR_INVALID;
+  return BOS_OK;
+}
+
+// Writes the descriptors of `sel` (synchronous copy from host memory).
+bos_status batch_prepare(const BatchIn& b, const BatchLayout& L, char* ws, const std::vector<uint32_t>& sel,
+                         const std::vector<uint32_t>& attempt, std::vector<BatchLaunch>* launches,
+                         cudaStream_t st) {
+  std::vector<char> desc;
+  bos_status s = batch_build(b, L, ws, sel, attempt, launches, &desc);
+  if (s != BOS_OK) return s;
+  BOS_CUDA(cudaMemcpyAsync(ws + L.desc_off, desc.data(), desc.size(), cudaMemcpyHostToDevice, st));
+  BOS_CUDA(cudaStreamSynchronize(st));
+  return BOS_OK;
+}
+
+std::vector<uint32_t> all_arrays(uint32_t num) {
+  std::vector<uint32_t> v(num);
+  for (uint32_t j = 0; j < num; ++j) v[j] = j;
+  return v;
+}
+
+// After an enqueue: reads every array's flags; arrays that overflowed run again (as a smaller
+// batch) with the next attempt counter, up to max_attempts; then the descriptors of the full
+// batch (attempt 0) are written back so a captured graph stays valid.
+bos_status batch_collect(const BatchIn& b, const BatchLayout& L, char* ws, cudaStream_t st, uint32_t* h_attempts) {
+  const uint32_t max_attempts = b.base.max_attempts ? b.base.max_attempts : kDefaultAttempts;
+  std::vector<uint32_t> attempt(b.num, 0);
+  std::vector<Ctrl> h(b.num);
+  std::vector<uint32_t> sel = all_arrays(b.num), launched_retry;
+  bos_status result = BOS_OK;
+  for (uint32_t round = 0;; ++round) {
+    if (b.num) BOS_CUDA(cudaMemcpyAsync(h.data(), ws + L.ctrl_off, b.num * sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    BOS_CUDA(cudaStreamSynchronize(st));
+    std::vector<uint32_t> failed;
+    for (uint32_t j : sel) {
+      if (L.arr[j].pl.n == 0) continue;
+      if (h[j].timeout) result = BOS_ERR_TIMEOUT;
+      if (h[j].overflow) failed.push_back(j);
+    }
+    if (result != BOS_OK || failed.empty()) break;
+    for (uint32_t j : failed) attempt[j]++;
+    bool exhausted = false;
+    for (uint32_t j : failed) exhausted |= attempt[j] >= max_attempts;
+    if (exhausted) {
+      result = BOS_ERR_OVERFLOW;
+      break;
+    }
+    std::vector<BatchLaunch> launches;
+    bos_status s = batch_prepare(b, L, ws, failed, attempt, &launches, st);
+    if (s != BOS_OK) return s;
+    if ((s = batch_enqueue(L, ws, launches, st)) != BOS_OK) return s;
+    sel = failed;
+    launched_retry = failed;
+  }
+  if (h_attempts)
+    for (uint32_t j = 0; j < b.num; ++j) h_attempts[j] = L.arr[j].pl.n ? attempt[j] + 1 : 0;
+  if (!launched_retry.empty()) {  // restore the full batch's descriptors
+    std::vector<BatchLaunch> launches;
+    const bos_status s = batch_prepare(b, L, ws, all_arrays(b.num), std::vector<uint32_t>(b.num, 0), &launches, st);
+    if (s != BOS_OK) return s;
+  }
+  return result;
+}
+
 }  // namespace
 
 size_t orp_workspace_bytes(uint64_t n, const bos_params* p) {
@@ -495,37 +804,67 @@ bos_status bos_sort(const void* d_in, void* d_out, uint64_t n, const bos_params*
 }
 
 size_t bos_batched_workspace_bytes(const uint64_t* h_offsets, uint32_t num, const uint32_t* h_Z,
-                                   const bos_params* base) {
-  if (!h_offsets || !base) return 0;
-  size_t best = 0;
-  for (uint32_t j = 0; j < num; ++j) {
-    bos_params p = *base;
-    if (h_Z) p.Z = h_Z[j];
-    const size_t w = bos_workspace_bytes(h_offsets[j + 1] - h_offsets[j], &p);
-    best = w > best ? w : best;
-  }
-  return best;
+                                   const uint8_t* h_ops, const bos_params* base) {
+  if (!h_offsets || !base || (num && !h_ops)) return 0;
+  std::vector<uint64_t> seeds(num, 0);
+  BatchIn b{nullptr, nullptr, h_offsets, num, seeds.data(), h_Z, h_ops, *base};
+  BatchLayout L;
+  if (batch_layout(b, &L) != BOS_OK) return 0;
+  return L.total;
+}
+
+bos_status bos_batched_prepare(const void* d_in, void* d_out, const uint64_t* h_offsets, uint32_t num,
+                               const uint64_t* h_seeds, const uint32_t* h_Z, const uint8_t* h_ops,
+                               const bos_params* base, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!base) return BOS_ERR_INVALID;
+  BatchIn b{d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, *base};
+  BatchLayout L;
+  bos_status s = batch_layout(b, &L);
+  if (s != BOS_OK) return s;
+  if ((s = batch_check_in(b, L, d_ws, ws_bytes)) != BOS_OK) return s;
+  std::vector<BatchLaunch> launches;
+  return batch_prepare(b, L, (char*)d_ws, all_arrays(num), std::vector<uint32_t>(num, 0), &launches,
+                       (cudaStream_t)stream);
+}
+
+bos_status bos_batched_enqueue(const void* d_in, void* d_out, const uint64_t* h_offsets, uint32_t num,
+                               const uint64_t* h_seeds, const uint32_t* h_Z, const uint8_t* h_ops,
+                               const bos_params* base, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!base) return BOS_ERR_INVALID;
+  BatchIn b{d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, *base};
+  BatchLayout L;
+  bos_status s = batch_layout(b, &L);
+  if (s != BOS_OK) return s;
+  if ((s = batch_check_in(b, L, d_ws, ws_bytes)) != BOS_OK) return s;
+  std::vector<BatchLaunch> launches;
+  if ((s = batch_build(b, L, (char*)d_ws, all_arrays(num), std::vector<uint32_t>(num, 0), &launches, nullptr)) != BOS_OK)
+    return s;
+  return batch_enqueue(L, (char*)d_ws, launches, (cudaStream_t)stream);
+}
+
+bos_status bos_batched_collect(const void* d_in, void* d_out, const uint64_t* h_offsets, uint32_t num,
+                               const uint64_t* h_seeds, const uint32_t* h_Z, const uint8_t* h_ops,
+                               const bos_params* base, void* d_ws, size_t ws_bytes, void* stream,
+                               uint32_t* h_attempts) {
+  if (!base) return BOS_ERR_INVALID;
+  BatchIn b{d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, *base};
+  BatchLayout L;
+  bos_status s = batch_layout(b, &L);
+  if (s != BOS_OK) return s;
+  if ((s = batch_check_in(b, L, d_ws, ws_bytes)) != BOS_OK) return s;
+  return batch_collect(b, L, (char*)d_ws, (cudaStream_t)stream, h_attempts);
 }
 
 bos_status bos_sort_batched(const void* d_in, void* d_out, const uint64_t* h_offsets, uint32_t num,
                             const uint64_t* h_seeds, const uint32_t* h_Z, const uint8_t* h_ops,
                             const bos_params* base, void* d_ws, size_t ws_bytes, void* stream,
                             uint32_t* h_attempts) {
-  if (!h_offsets || !h_seeds || !h_ops || !base) return BOS_ERR_INVALID;
-  for (uint32_t j = 0; j < num; ++j) {
-    if (h_offsets[j + 1] < h_offsets[j]) return BOS_ERR_INVALID;
-    bos_params p = *base;
-    p.seed = h_seeds[j];
-    if (h_Z) p.Z = h_Z[j];
-    const uint64_t n = h_offsets[j + 1] - h_offsets[j];
-    const size_t off = h_offsets[j] * base->rec_bytes;
-    bos_info info{};
-    const bos_status s = run((const char*)d_in + off, (char*)d_out + off, n, &p, d_ws, ws_bytes, stream,
-                             &info, h_ops[j] != 0);
-    if (h_attempts) h_attempts[j] = info.attempts;
-    if (s != BOS_OK) return s;
-  }
-  return BOS_OK;
+  bos_status s = bos_batched_prepare(d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, base, d_ws, ws_bytes, stream);
+  if (s != BOS_OK) return s;
+  s = bos_batched_enqueue(d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, base, d_ws, ws_bytes, stream);
+  if (s != BOS_OK) return s;
+  return bos_batched_collect(d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, base, d_ws, ws_bytes, stream,
+                             h_attempts);
 }
 
 bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t rec_bytes,

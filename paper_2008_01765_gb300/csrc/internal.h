@@ -32,6 +32,16 @@ struct PassArgs {
 };
 
 uint32_t orp_smem_bytes(int R, uint32_t Z, uint32_t k, bool last);
+
+// One launch of the one-CTA-per-subproblem pass over many arrays (batched ORP).
+struct BatchPass {
+  const PassArgs* args;   // device: one entry per array in this launch
+  const uint64_t* first;  // device: running sum of subproblem counts, narr + 1 entries
+  uint32_t narr;
+  uint64_t nblocks;       // = first[narr]
+  uint32_t* ticket;       // device: zeroed counter (LAST passes)
+};
+cudaError_t launch_orp_pass_batched(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st, int R);
 cudaError_t launch_orp_pass(const PassArgs& a, int mode, uint64_t grid, cudaStream_t st, int R,
                             bool trace);
 
@@ -55,6 +65,16 @@ struct RadixArgs {
   uint32_t ticket_base;
 };
 uint64_t radix_tiles(uint64_t n, int R);
+// Radix stages over many arrays in one launch (batched sort).
+struct BatchRadix {
+  const RadixArgs* args;  // device: one entry per array
+  const uint64_t* first;  // device: running sum of tiles (kTile records each), narr + 1 entries
+  uint32_t narr;
+  uint64_t nblocks;       // = first[narr]
+  uint32_t* ticket;       // device: one zeroed counter per digit
+};
+// stage 0 = histograms, 1 = digit offsets, 2 = the pass of `digit`
+cudaError_t launch_radix_batched(const BatchRadix& br, int R, int stage, uint32_t digit, cudaStream_t st);
 cudaError_t launch_radix_hist(const RadixArgs& a, int R, cudaStream_t st);
 cudaError_t launch_radix_prep(const RadixArgs& a, int R, cudaStream_t st);
 cudaError_t launch_radix_pass(const RadixArgs& a, int R, uint32_t digit, cudaStream_t st);

@@ -73,8 +73,9 @@ __device__ __forceinline__ void load_rec(typename RecT<R>::T& dst, const void* b
   dst = reinterpret_cast<const typename RecT<R>::T*>(base)[idx];
 }
 
+// One subproblem q of one pass (the whole CTA).
 template <int R, int MODE, bool TRACE>
-__global__ void __launch_bounds__(kThreads, 1) orp_pass_kernel(PassArgs a) {
+__device__ __forceinline__ void orp_pass_body(const PassArgs& a, uint64_t q) {
   using Rec = typename RecT<R>::T;
   constexpr bool FIRST = MODE & kModeFirst;
   constexpr bool LAST = MODE & kModeLast;
@@ -93,16 +94,6 @@ __global__ void __launch_bounds__(kThreads, 1) orp_pass_kernel(PassArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t wstride = D + 1;
 
-  // Subproblem index. The LAST pass takes it from a ticket so that every look-back predecessor
-  // has already started (no CTA waits on one that is not yet resident).
-  uint64_t q;
-  if constexpr (LAST) {
-    if (tid == 0) misc[0] = atomicAdd(&a.ctrl->tickets[a.ticket_slot], 1u);
-    __syncthreads();
-    q = misc[0];
-  } else {
-    q = blockIdx.x;
-  }
   const uint32_t i = a.i;
   const uint64_t t = q & ((1ull << i) - 1);
   const uint64_t G = q >> i;
@@ -333,6 +324,42 @@ __global__ void __launch_bounds__(kThreads, 1) orp_pass_kernel(PassArgs a) {
   }
 }
 
+// Single array: one CTA per subproblem; the LAST pass takes subproblems by ticket so that every
+// look-back predecessor has already started (no CTA waits on one that is not yet resident).
+template <int R, int MODE, bool TRACE>
+__global__ void __launch_bounds__(kThreads, 1) orp_pass_kernel(PassArgs a) {
+  __shared__ unsigned long long q_s;
+  uint64_t q = blockIdx.x;
+  if constexpr ((MODE & kModeLast) != 0) {
+    if (threadIdx.x == 0) q_s = atomicAdd(&a.ctrl->tickets[a.ticket_slot], 1u);
+    __syncthreads();
+    q = q_s;
+  }
+  orp_pass_body<R, MODE, TRACE>(a, q);
+}
+
+// Many arrays in one launch: block (or ticket) b is subproblem b - first[j] of array j, where
+// first[] holds the running sum of the arrays' subproblem counts. LAST passes take tickets over
+// the whole launch, so inside every array the subproblems start in order.
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) orp_pass_batched_kernel(BatchPass bp) {
+  __shared__ unsigned long long q_s;
+  __shared__ uint32_t j_s;
+  if (threadIdx.x == 0) {
+    const uint64_t t = (MODE & kModeLast) ? (uint64_t)atomicAdd(bp.ticket, 1u) : (uint64_t)blockIdx.x;
+    uint32_t lo = 0, hi = bp.narr;  // largest j with first[j] <= t
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (bp.first[mid] <= t) lo = mid; else hi = mid;
+    }
+    j_s = lo;
+    q_s = t - bp.first[lo];
+  }
+  __syncthreads();
+  const PassArgs a = bp.args[j_s];
+  orp_pass_body<R, MODE, false>(a, q_s);
+}
+
 }  // namespace
 
 uint32_t orp_smem_bytes(int R, uint32_t Z, uint32_t k, bool last) {
@@ -356,6 +383,33 @@ static cudaError_t launch_r(const PassArgs& a, int mode, uint64_t grid, cudaStre
     case kModeFirst: return launch_mode<R, kModeFirst, TRACE>(a, grid, st);
     case kModeLast: return launch_mode<R, kModeLast, TRACE>(a, grid, st);
     default: return launch_mode<R, kModeFirst | kModeLast, TRACE>(a, grid, st);
+  }
+}
+
+template <int R, int MODE>
+static cudaError_t batched_mode(const BatchPass& bp, uint32_t smem, cudaStream_t st) {
+  auto kern = orp_pass_batched_kernel<R, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)bp.nblocks, kThreads, smem, st>>>(bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orp_pass_batched(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st, int R) {
+  if (bp.nblocks == 0) return cudaSuccess;
+  if (R == 8) {
+    switch (mode) {
+      case 0: return batched_mode<8, 0>(bp, smem, st);
+      case kModeFirst: return batched_mode<8, kModeFirst>(bp, smem, st);
+      case kModeLast: return batched_mode<8, kModeLast>(bp, smem, st);
+      default: return batched_mode<8, kModeFirst | kModeLast>(bp, smem, st);
+    }
+  }
+  switch (mode) {
+    case 0: return batched_mode<16, 0>(bp, smem, st);
+    case kModeFirst: return batched_mode<16, kModeFirst>(bp, smem, st);
+    case kModeLast: return batched_mode<16, kModeLast>(bp, smem, st);
+    default: return batched_mode<16, kModeFirst | kModeLast>(bp, smem, st);
   }
 }
 

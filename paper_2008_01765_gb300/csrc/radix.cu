@@ -19,16 +19,16 @@ constexpr int kItems = 8;
 constexpr uint32_t kTile = kThreads * kItems;
 constexpr int kHistCtas = 4 * 152;
 
+// Counts of every 8-bit digit of the keys in records [lo, hi), added to a.hist.
 template <int R>
-__global__ void __launch_bounds__(kThreads) radix_hist_kernel(RadixArgs a) {
+__device__ __forceinline__ void radix_hist_body(const RadixArgs& a, uint64_t lo, uint64_t hi, uint64_t step) {
   using Rec = typename RecT<R>::T;
   constexpr int D = RecT<R>::kDigits;
   __shared__ uint32_t h[D][256];
   for (int x = threadIdx.x; x < D * 256; x += kThreads) (&h[0][0])[x] = 0;
   __syncthreads();
   const Rec* in = reinterpret_cast<const Rec*>(a.in);
-  for (uint64_t idx = (uint64_t)blockIdx.x * kThreads + threadIdx.x; idx < a.n;
-       idx += (uint64_t)gridDim.x * kThreads) {
+  for (uint64_t idx = lo + threadIdx.x; idx < hi; idx += step) {
     const auto key = RecT<R>::key(in[idx]);
 #pragma unroll
     for (int d = 0; d < D; ++d) atomicAdd(&h[d][(key >> (8 * d)) & 255u], 1u);
@@ -40,12 +40,38 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(RadixArgs a) {
   }
 }
 
-// Per digit: exclusive offsets of the 256 digit values, and whether the digit is live.
 template <int R>
-__global__ void __launch_bounds__(256) radix_prep_kernel(RadixArgs a) {
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(RadixArgs a) {
+  // grid-stride over the whole array: block b handles b*kThreads + j*gridDim*kThreads + tid
+  const uint64_t step = (uint64_t)gridDim.x * kThreads;
+  radix_hist_body<R>(a, (uint64_t)blockIdx.x * kThreads, a.n, step);
+}
+
+// Batched: block b counts chunk b - first[j] (kTile records) of array j.
+template <int R>
+__global__ void __launch_bounds__(kThreads) radix_hist_batched_kernel(BatchRadix br) {
+  __shared__ uint32_t j_s;
+  __shared__ unsigned long long c_s;
+  if (threadIdx.x == 0) {
+    uint32_t lo = 0, hi = br.narr;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (br.first[mid] <= blockIdx.x) lo = mid; else hi = mid;
+    }
+    j_s = lo;
+    c_s = blockIdx.x - br.first[lo];
+  }
+  __syncthreads();
+  const RadixArgs& a = br.args[j_s];
+  const uint64_t lo = c_s * kTile, hi = lo + kTile < a.n ? lo + kTile : a.n;
+  radix_hist_body<R>(a, lo, hi, kThreads);
+}
+
+// Per digit: exclusive offsets of the 256 digit values, and whether the digit is live.
+__device__ __forceinline__ void radix_prep_body(const RadixArgs& a, int d) {
   __shared__ uint32_t s[256];
   __shared__ uint32_t any_full;
-  const int d = blockIdx.x, v = threadIdx.x;
+  const int v = threadIdx.x;
   const uint32_t c = a.hist[d * 256 + v];
   s[v] = c;
   if (v == 0) any_full = 0;
@@ -63,10 +89,22 @@ __global__ void __launch_bounds__(256) radix_prep_kernel(RadixArgs a) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads, 2) radix_pass_kernel(RadixArgs a, uint32_t digit) {
+__global__ void __launch_bounds__(256) radix_prep_kernel(RadixArgs a) {
+  radix_prep_body(a, blockIdx.x);
+}
+
+// Batched: block b = (array b / D, digit b % D).
+template <int R>
+__global__ void __launch_bounds__(256) radix_prep_batched_kernel(BatchRadix br) {
+  constexpr int D = RecT<R>::kDigits;
+  radix_prep_body(br.args[blockIdx.x / D], blockIdx.x % D);
+}
+
+// One tile of one live digit (the whole CTA).
+template <int R>
+__device__ __forceinline__ void radix_pass_body(const RadixArgs& a, uint32_t digit, uint64_t tile) {
   using Rec = typename RecT<R>::T;
   const uint32_t live = a.ctrl->radix_live;
-  if (!((live >> digit) & 1u)) return;
   // Buffer chain: X_nlive = buf0 (output); X_j alternates backwards. This pass maps X_c -> X_c+1.
   const uint32_t nlive = __popc(live);
   const uint32_t c = __popc(live & ((1u << digit) - 1));
@@ -84,10 +122,9 @@ __global__ void __launch_bounds__(kThreads, 2) radix_pass_kernel(RadixArgs a, ui
   uint32_t* misc = reinterpret_cast<uint32_t*>(gstart + 256);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) misc[0] = atomicAdd(&a.ctrl->tickets[a.ticket_base + digit], 1u);
+  (void)misc;
   for (int x = tid; x < kWarps * 257; x += kThreads) wcnt[x] = 0;
   __syncthreads();
-  const uint64_t tile = misc[0];
   const uint64_t t0 = tile * kTile;
   const uint32_t shift = 8 * digit;
   const uint32_t lt_mask = lanemask_lt();
@@ -183,6 +220,37 @@ __global__ void __launch_bounds__(kThreads, 2) radix_pass_kernel(RadixArgs a, ui
 }
 
 template <int R>
+__global__ void __launch_bounds__(kThreads, 2) radix_pass_kernel(RadixArgs a, uint32_t digit) {
+  __shared__ unsigned long long t_s;
+  if (!((a.ctrl->radix_live >> digit) & 1u)) return;
+  if (threadIdx.x == 0) t_s = atomicAdd(&a.ctrl->tickets[a.ticket_base + digit], 1u);
+  __syncthreads();
+  radix_pass_body<R>(a, digit, t_s);
+}
+
+// Batched: tickets over all tiles of all arrays; ticket t is tile t - first[j] of array j, so
+// inside every array the tiles start in order (the look-back stops at the array's tile 0).
+template <int R>
+__global__ void __launch_bounds__(kThreads, 2) radix_pass_batched_kernel(BatchRadix br, uint32_t digit) {
+  __shared__ unsigned long long t_s;
+  __shared__ uint32_t j_s;
+  if (threadIdx.x == 0) {
+    const uint64_t t = atomicAdd(br.ticket + digit, 1u);
+    uint32_t lo = 0, hi = br.narr;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (br.first[mid] <= t) lo = mid; else hi = mid;
+    }
+    j_s = lo;
+    t_s = t - br.first[lo];
+  }
+  __syncthreads();
+  const RadixArgs& a = br.args[j_s];
+  if (!((a.ctrl->radix_live >> digit) & 1u)) return;
+  radix_pass_body<R>(a, digit, t_s);
+}
+
+template <int R>
 uint32_t pass_smem() {
   using Rec = typename RecT<R>::T;
   return kTile * sizeof(Rec) + (kWarps * 257 + 258) * 4 + 256 * 8 + 64;
@@ -199,6 +267,36 @@ cudaError_t launch_radix_hist(const RadixArgs& a, int R, cudaStream_t st) {
     radix_hist_kernel<8><<<grid, kThreads, 0, st>>>(a);
   else
     radix_hist_kernel<16><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radix_batched(const BatchRadix& br, int R, int stage, uint32_t digit, cudaStream_t st) {
+  if (br.narr == 0) return cudaSuccess;
+  if (stage == 0) {  // histograms: one block per chunk of kTile records
+    if (br.nblocks == 0) return cudaSuccess;
+    if (R == 8)
+      radix_hist_batched_kernel<8><<<(unsigned)br.nblocks, kThreads, 0, st>>>(br);
+    else
+      radix_hist_batched_kernel<16><<<(unsigned)br.nblocks, kThreads, 0, st>>>(br);
+  } else if (stage == 1) {  // digit offsets
+    if (R == 8)
+      radix_prep_batched_kernel<8><<<br.narr * RecT<8>::kDigits, 256, 0, st>>>(br);
+    else
+      radix_prep_batched_kernel<16><<<br.narr * RecT<16>::kDigits, 256, 0, st>>>(br);
+  } else {  // one digit pass over every array's tiles
+    if (br.nblocks == 0) return cudaSuccess;
+    if (R == 8) {
+      const uint32_t sm = pass_smem<8>();
+      cudaError_t e = cudaFuncSetAttribute(radix_pass_batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      radix_pass_batched_kernel<8><<<(unsigned)br.nblocks, kThreads, sm, st>>>(br, digit);
+    } else {
+      const uint32_t sm = pass_smem<16>();
+      cudaError_t e = cudaFuncSetAttribute(radix_pass_batched_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      radix_pass_batched_kernel<16><<<(unsigned)br.nblocks, kThreads, sm, st>>>(br, digit);
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -280,3 +280,62 @@ def test_cfg3_geometry_plans(bos):
     got, info = gpu_sort(bos, recs, 1024, 5)
     np.testing.assert_array_equal(got, ref)
     assert 2 <= info.passes <= 5
+
+
+def _check_batch_against_oracle(recs, offs, seeds, ops, Zs, got, att):
+    for j in range(len(offs) - 1):
+        a, b = int(offs[j]), int(offs[j + 1])
+        f = oracle.sort if ops[j] else oracle.orp
+        ref, rinfo = f(recs[a:b], int(Zs[j]), int(seeds[j]), method=oracle.CLOSED)
+        assert att[j] == (rinfo.attempts if b > a else 0), j
+        np.testing.assert_array_equal(got[a:b], ref, err_msg=f"array {j}")
+
+
+def test_batched_graph_replay_equals_alone(bos):
+    # The launch sequence of a batch is captured once into a CUDA graph and replayed; every
+    # array's result equals that array run alone (oracle), for mixed sizes, ops and Z.
+    import torch
+    sizes = inputs.batched_sizes(64, 6, 17, seed=11)
+    sizes[3] = 0
+    recs, offs = inputs.make_batch(sizes, 8, seed=5)
+    seeds = np.arange(7, 7 + sizes.size, dtype=np.uint64) * 1000003
+    ops = (np.arange(sizes.size) % 3 != 0).astype(np.uint8)
+    Zs = np.array([[512, 1024, 256, 2048][j % 4] for j in range(sizes.size)], dtype=np.uint32)
+    x = bos.to_device(recs)
+    out = torch.empty_like(x)
+    batch = bos.Batch(x, out, offs, seeds, ops, bos.params(8, 512, 0), Zs=Zs)
+    batch.prepare()
+    stream = torch.cuda.Stream()
+    batch.enqueue(stream)  # warm-up outside the capture
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        batch.enqueue(stream)
+    out.zero_()
+    graph.replay()
+    att = batch.collect(stream)
+    _check_batch_against_oracle(recs, offs, seeds, ops, Zs, bos.to_host(out, recs.dtype), att)
+    out.zero_()
+    graph.replay()  # a second replay gives the same result
+    att2 = batch.collect(stream)
+    np.testing.assert_array_equal(att2, att)
+    _check_batch_against_oracle(recs, offs, seeds, ops, Zs, bos.to_host(out, recs.dtype), att2)
+
+
+def test_batched_retries_only_overflowing_arrays(bos):
+    # Z = 32 with 4096 records overflows in about 14% of attempts: such arrays rerun with the next
+    # attempt counter and still match the oracle; the others keep attempt 1.
+    import torch
+    sizes = np.full(24, 4096, dtype=np.int64)
+    recs, offs = inputs.make_batch(sizes, 16, seed=8)
+    seeds = np.arange(24, dtype=np.uint64)
+    ops = np.ones(24, dtype=np.uint8)
+    Zs = np.full(24, 32, dtype=np.uint32)
+    x = bos.to_device(recs)
+    out = torch.empty_like(x)
+    try:
+        att = bos.sort_batched(x, out, offs, seeds, ops, bos.params(16, 32, 0, max_attempts=16), Zs=Zs)
+    except bos.BosError as e:
+        pytest.skip(f"an array exhausted its attempts: {e}")
+    assert (att >= 1).all() and (att > 1).any()
+    _check_batch_against_oracle(recs, offs, seeds, ops, Zs, bos.to_host(out, recs.dtype), att)
