@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="bos_params.flags (comparisons)")
     ap.add_argument("--k", type=int, default=0, help="levels per ORP pass (0 = automatic)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving"],
+                    help="sort: n=2^30 16-B records (the headline); batched: 4096 arrays of 2^10..2^20 "
+                         "8-B records in one CUDA graph; serving: a Poisson request stream")
     return ap.parse_args()
 
 
@@ -201,10 +204,183 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_step_bytes(offs, Zs, R=8):
+    """Algorithmic HBM bytes of one batched sort: per array, its ORP passes as the batched
+    (one-CTA-per-subproblem) kernel plans them - input and output records once, the B*Z slot
+    array written and read between passes - plus the radix histogram and its live digit passes
+    (4 for uniform 32-bit keys)."""
+    from paper_2008_01765_gb300 import bos
+    total, cache = 0.0, {}
+    for j in range(len(offs) - 1):
+        n = int(offs[j + 1] - offs[j])
+        if n == 0:
+            continue
+        key = (n, int(Zs[j]))
+        if key not in cache:
+            info = bos.plan(n, R, int(Zs[j]), flags=bos.FLAG_GENERIC)
+            slot = info.B * int(Zs[j]) * (R + 4)
+            cache[key] = 2 * n * R + 2 * (info.passes - 1) * slot + n * 4 + 4 * 2 * n * R
+        total += cache[key]
+    return total
+
+
+def run_batched(args):
+    import torch
+    from paper_2008_01765_gb300 import _build
+    _build.build()
+    from paper_2008_01765_gb300 import autotune, bos, inputs
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = inputs.batched_sizes(4096, 10.0, 20.0, seed=1 + rank)
+    recs, offs = inputs.make_batch(sizes, 8, seed=1 + rank)
+    Zs = autotune.z_array(sizes, 8)
+    seeds = np.arange(1, sizes.size + 1, dtype=np.uint64)
+    ops = np.ones(sizes.size, dtype=np.uint8)
+    host_in = torch.from_numpy(recs.view(np.uint8).reshape(-1))
+    x = host_in.to(dev)
+    out = torch.empty_like(x)
+    batch = bos.Batch(x, out, offs, seeds, ops, bos.params(8, 512, 0), Zs=Zs)
+    stream = torch.cuda.Stream(dev)
+    batch.prepare(stream)
+    batch.enqueue(stream)
+    batch.collect(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        batch.enqueue(stream)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            graph.replay()
+        batch.collect(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            graph.replay()  # the graph's work is on `stream`, between the events
+        att = batch.collect(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps, dev)
+    n_total = int(offs[-1])
+    hbm, _ = peaks()
+    step_bytes = batched_step_bytes(offs, Zs)
+    line = {"metric": "records/sec, batched bucket oblivious sort (4096 arrays, CUDA graph)",
+            "value": world * n_total / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batched sort, 4096 arrays, n_j = floor(2^U), U ~ U[10, 20], 8-B records "
+                                   "{u32 key uniform, u32 payload}, Z per size class from the autotune table",
+                       "records": n_total, "arrays": int(sizes.size), "Z_values": sorted(set(int(z) for z in Zs)),
+                       "attempts_max": int(att.max()), "l2": "batch (%.1f GiB) larger than L2" % (n_total * 8 / 2**30)},
+            "hbm_gbs": step_bytes / (ms / 1e3) / 1e9, "hbm_frac": step_bytes / (ms / 1e3) / 1e9 / hbm,
+            "clocks": clk}
+    if not args.no_e2e:
+        pin_in = host_in.pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(max(1, min(args.steps, 3))):
+            with torch.cuda.stream(stream):
+                x.copy_(pin_in, non_blocking=True)
+                graph.replay()
+            batch.collect(stream)
+            with torch.cuda.stream(stream):
+                pin_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, 3))
+        ems = e0.elapsed_time(e1) / k
+        line["e2e"] = {"value": world * n_total / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n_total * 8,
+                       "d2h_bytes_per_step": n_total * 8, "ms_per_step": ems}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson stream of ORP and sort requests (50/50), n log-uniform in [2^12, 2^26], 16-B
+    records {u64 key uniform, u64 payload}, 64 GiB admission budget. The arrival rate is 70% of
+    the capacity measured by a burst of the same requests first."""
+    import threading
+    import torch
+    from paper_2008_01765_gb300 import _build
+    _build.build()
+    from paper_2008_01765_gb300 import inputs, serve
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    pool = inputs.make_records(1 << 26, 16, "uniform", seed=7 + rank, payload="random")
+    count = max(40, args.steps * 40)
+    arrivals, sizes, ops, seeds = inputs.poisson_stream(count, 1.0, 12.0, 26.0, seed=3 + rank)
+    rng = np.random.default_rng(5 + rank)
+    offs = [int(rng.integers(0, pool.size - n + 1)) for n in sizes]
+    jobs = [(pool[o:o + int(n)], int(op), int(sd)) for o, n, op, sd in zip(offs, sizes, ops, seeds)]
+
+    def make_server():
+        return serve.Server(budget_bytes=64 << 30, workers=4, rec_bytes=16,
+                            executor_factory=lambda: serve.CudaExecutor(f"cuda:{local}", keep_results=False))
+
+    # capacity: the whole stream submitted at once
+    srv = make_server()
+    for recs, op, sd in jobs[: min(len(jobs), 16)]:  # warm-up (allocator, kernels)
+        srv.submit(recs, op=op, seed=sd)
+    srv.close()
+    srv = make_server()
+    t0 = time.perf_counter()
+    reqs = [srv.submit(recs, op=op, seed=sd) for recs, op, sd in jobs]
+    try:
+        for r in reqs:
+            r.wait(600)
+    finally:
+        srv.close()
+    t1 = time.perf_counter()
+    capacity_jobs = len(jobs) / (t1 - t0)
+    rate = 0.7 * capacity_jobs
+    # the Poisson stream at 70% of that capacity
+    srv = make_server()
+    clocks = ClockSampler(local)
+    clocks.start()
+    reqs = []
+    start = time.perf_counter()
+    for (recs, op, sd), ta in zip(jobs, arrivals / rate):
+        delay = start + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        reqs.append(srv.submit(recs, op=op, seed=sd))
+    try:
+        for r in reqs:
+            r.wait(600)
+    finally:
+        srv.close()
+    clk = clocks.stop()
+    st = srv.stats()
+    line = {"metric": "records/sec and p50/p99 latency, serving a Poisson stream of ORP/sort requests",
+            "value": st["records_per_s"] * world, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "config": {"workload": "serving: Poisson arrivals, 50/50 ORP/sort, n log-uniform in [2^12, 2^26], "
+                                   "16-B records, 64 GiB admission budget, 4 worker streams",
+                       "requests": st["requests"], "records": st["records"],
+                       "arrival_rate_per_s": rate, "capacity_requests_per_s": capacity_jobs,
+                       "capacity_records_per_s": sum(int(n) for n in sizes) / (t1 - t0),
+                       "batched_requests": st["batched_requests"], "peak_held_bytes": st["peak_held_bytes"]},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
     from paper_2008_01765_gb300 import _build
     _build.build()

@@ -61,6 +61,9 @@ typedef enum {
 #define BOS_FLAG_GENERIC 0x2u
 /* Do not use thread-block clusters (C = 1): fewer levels per pass, same result. */
 #define BOS_FLAG_NO_CLUSTER 0x4u
+/* Fill *info with the plan for these arguments (B, L, passes, k, cluster size) and return
+ * without touching the device (pointers may be NULL). */
+#define BOS_FLAG_PLAN_ONLY 0x10u
 /* Plan the fewest passes (largest clusters) instead of the measured-cost plan; same result. */
 #define BOS_FLAG_FEWEST_PASSES 0x8u
 /* Largest thread-block cluster a pass may use (1, 2, 4, 8 or 16; 0 = the library's choice).

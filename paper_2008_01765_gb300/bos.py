@@ -17,6 +17,7 @@ FLAG_SKIP_PUBLISH = 0x1
 FLAG_GENERIC = 0x2
 FLAG_NO_CLUSTER = 0x4
 FLAG_FEWEST_PASSES = 0x8
+FLAG_PLAN_ONLY = 0x10
 
 
 def FLAG_FORCE_OVERFLOW(n):
@@ -108,6 +109,15 @@ def status_str(s):
 
 def params(rec_bytes=16, Z=512, seed=1, k=0, max_attempts=0, flags=0):
     return Params(rec_bytes, 4 if rec_bytes == 8 else 8, Z, k, max_attempts, flags, seed)
+
+
+def plan(n, rec_bytes=16, Z=512, k=0, flags=0, sort=True) -> Info:
+    """The library's pass plan for n records (no device work)."""
+    p = params(rec_bytes, Z, 0, k, 0, flags | FLAG_PLAN_ONLY)
+    info = Info()
+    fn = lib().bos_sort if sort else lib().bos_orp
+    _check(fn(None, None, n, ctypes.byref(p), None, 0, None, ctypes.byref(info)), "plan")
+    return info
 
 
 def workspace_bytes(n, p: Params) -> int:

@@ -10,7 +10,7 @@
 namespace bos {
 namespace {
 
-constexpr uint32_t kMaxSmem = 232448;  // opt-in dynamic shared memory per CTA on sm_100/103
+constexpr uint32_t kMaxSmem = 232448 - 1024;  // opt-in shared memory per CTA (sm_100/103) less static use
 constexpr uint32_t kMaxK = 6;          // per-pass digit-count table is (2^k)^2 words
 constexpr uint32_t kMaxPasses = 32;
 constexpr uint32_t kDefaultAttempts = 8;
@@ -337,7 +337,8 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, void* d_ws,
                size_t ws_bytes, void* stream, bos_info* info, bool sort) {
   Plan pl;
-  bos_status s = n ? device_plan(n, p, sort, &pl) : make_plan(n, p, sort, &pl);
+  const bool plan_only = p && (p->flags & BOS_FLAG_PLAN_ONLY);
+  bos_status s = (n && !plan_only) ? device_plan(n, p, sort, &pl) : make_plan(n, p, sort, &pl);
   if (s != BOS_OK) return s;
   if (info) {
     info->attempts = 0;
@@ -352,7 +353,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       info->max_k = pl.pass_k[x] > info->max_k ? pl.pass_k[x] : info->max_k;
     }
   }
-  if (n == 0) return BOS_OK;
+  if (n == 0 || plan_only) return BOS_OK;
   const size_t bytes = n * pl.R;
   if (!d_in || !d_out || !d_ws) return BOS_ERR_INVALID;
   if (((uintptr_t)d_in % pl.R) || ((uintptr_t)d_out % pl.R) || ((uintptr_t)d_ws & 255)) return BOS_ERR_INVALID;

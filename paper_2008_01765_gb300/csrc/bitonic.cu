@@ -84,9 +84,9 @@ cudaError_t run(const void* in, void* out, uint64_t n, cudaStream_t st) {
   using Rec = typename RecT<R>::T;
   const uint32_t bs = (uint32_t)(n < kBlock ? n : kBlock);
   const uint32_t smem = bs * sizeof(Rec);
-  cudaError_t e = cudaFuncSetAttribute(bitonic_block_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_optin(bitonic_block_kernel<R, true>);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(bitonic_block_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = set_smem_optin(bitonic_block_kernel<R, false>);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)(n / bs);
   bitonic_block_kernel<R, true><<<blocks, kThreads, smem, st>>>(in, out, bs, 0);

@@ -9,6 +9,21 @@ namespace bos {
 
 constexpr uint32_t kDummy = 0xFFFFFFFFu;  // tag of a dummy slot; real tags are labels < 2^31
 
+// Dynamic shared memory limit of every kernel that may use more than 48 KB: the device's opt-in
+// maximum minus the kernel's static shared memory - one value per kernel, never the launch's own
+// size. The attribute is per-function process state, and host threads launching the same kernel
+// with different sizes must not lower it under one another.
+template <typename Kernel>
+inline cudaError_t set_smem_optin(Kernel kern) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011). Ten rounds; each multiplies counter words 0 and 2 by
 // the two round multipliers, xors the high halves into words 1 and 3 with the round key, and

@@ -370,7 +370,7 @@ template <int R, int MODE, bool TRACE>
 static cudaError_t launch_mode(const PassArgs& a, uint64_t grid, cudaStream_t st) {
   const uint32_t smem = smem_layout(R, a.Z, a.k, MODE & kModeLast).total;
   auto kern = orp_pass_kernel<R, MODE, TRACE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_optin(kern);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -389,7 +389,7 @@ static cudaError_t launch_r(const PassArgs& a, int mode, uint64_t grid, cudaStre
 template <int R, int MODE>
 static cudaError_t batched_mode(const BatchPass& bp, uint32_t smem, cudaStream_t st) {
   auto kern = orp_pass_batched_kernel<R, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_optin(kern);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)bp.nblocks, kThreads, smem, st>>>(bp);
   return cudaGetLastError();

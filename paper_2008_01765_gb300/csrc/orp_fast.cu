@@ -605,7 +605,7 @@ template <int R, int MODE, bool CL, bool TRACE>
 static cudaError_t fast_launch_mode(const PassArgs& a, uint32_t C, uint32_t max_clusters, cudaStream_t st) {
   const uint32_t smem = fast_layout(R, a.Z, a.k, C, MODE & kModeLast).total;
   auto kern = orp_fast_kernel<R, MODE, CL, TRACE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_optin(kern);
   if (e != cudaSuccess) return e;
   const uint64_t nsub = a.B >> a.k;
   cudaLaunchConfig_t cfg{};
@@ -661,7 +661,7 @@ template <int R, int MODE, bool CL>
 static int fast_occupancy(uint32_t Z, uint32_t k, uint32_t C) {
   const uint32_t smem = fast_layout(R, Z, k, C, MODE & kModeLast).total;
   auto kern = orp_fast_kernel<R, MODE, CL, false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (set_smem_optin(kern) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }

@@ -287,12 +287,12 @@ cudaError_t launch_radix_batched(const BatchRadix& br, int R, int stage, uint32_
     if (br.nblocks == 0) return cudaSuccess;
     if (R == 8) {
       const uint32_t sm = pass_smem<8>();
-      cudaError_t e = cudaFuncSetAttribute(radix_pass_batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaError_t e = set_smem_optin(radix_pass_batched_kernel<8>);
       if (e != cudaSuccess) return e;
       radix_pass_batched_kernel<8><<<(unsigned)br.nblocks, kThreads, sm, st>>>(br, digit);
     } else {
       const uint32_t sm = pass_smem<16>();
-      cudaError_t e = cudaFuncSetAttribute(radix_pass_batched_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaError_t e = set_smem_optin(radix_pass_batched_kernel<16>);
       if (e != cudaSuccess) return e;
       radix_pass_batched_kernel<16><<<(unsigned)br.nblocks, kThreads, sm, st>>>(br, digit);
     }
@@ -313,12 +313,12 @@ cudaError_t launch_radix_pass(const RadixArgs& a, int R, uint32_t digit, cudaStr
   if (grid == 0) return cudaSuccess;
   if (R == 8) {
     const uint32_t sm = pass_smem<8>();
-    cudaError_t e = cudaFuncSetAttribute(radix_pass_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = set_smem_optin(radix_pass_kernel<8>);
     if (e != cudaSuccess) return e;
     radix_pass_kernel<8><<<grid, kThreads, sm, st>>>(a, digit);
   } else {
     const uint32_t sm = pass_smem<16>();
-    cudaError_t e = cudaFuncSetAttribute(radix_pass_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = set_smem_optin(radix_pass_kernel<16>);
     if (e != cudaSuccess) return e;
     radix_pass_kernel<16><<<grid, kThreads, sm, st>>>(a, digit);
   }
