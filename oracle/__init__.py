@@ -54,6 +54,8 @@ def lib():
         L.or_sort.argtypes = [_vp, _vp, _u64, _u32, _u32, _u32, _u64, _u32, ctypes.c_int,
                               ctypes.c_int, ctypes.POINTER(OrpInfo)]
         L.or_sort.restype = ctypes.c_int
+        L.or_orp_sample.argtypes = [_u64, _u32, _u64, _u32, _vp, _u32, _vp, _vp, _vp, _u64]
+        L.or_orp_sample.restype = ctypes.c_int
         L.or_bitonic_sort.argtypes = [_vp, _u64, _u32, _u32]
         L.or_bitonic_sort.restype = ctypes.c_int
         _lib = L
@@ -154,6 +156,25 @@ def orp_many(recs, Z, seed0, count, max_attempts=8, method=LITERAL):
     if st != OK:
         raise OracleError(st)
     return out, att
+
+
+def orp_sample(n, Z, seed, buckets, attempt=0):
+    """Output offset, load and input indices (in output order) of the given final buckets of the
+    ORP of n records (no overflow check; for runs that reported none)."""
+    b = np.ascontiguousarray(buckets, dtype=np.uint64)
+    off = np.zeros(b.size, dtype=np.uint64)
+    load = np.zeros(b.size, dtype=np.uint32)
+    B, _ = geometry(n, Z)
+    cap = int(min(n, b.size * max(4 * n // max(B, 1), 16) + 64))
+    src = np.zeros(cap, dtype=np.uint64)
+    st = lib().or_orp_sample(n, Z, seed, attempt, _ptr(b), b.size, _ptr(off), _ptr(load), _ptr(src), cap)
+    if st != OK:
+        raise OracleError(st)
+    out, pos = [], 0
+    for x in range(b.size):
+        out.append(src[pos:pos + int(load[x])].copy())
+        pos += int(load[x])
+    return off, load, out
 
 
 def stable_sort(recs):

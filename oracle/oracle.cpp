@@ -369,6 +369,56 @@ int or_orp(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z
                      trace_cap, trace_len);
 }
 
+// Sampled ORP output at any size (Section 3.2 restated bucket by bucket, from the closed form of
+// the butterfly): for attempt `attempt`, final bucket b holds the elements labelled b in input
+// order; the output places bucket b at the sum of the loads of the buckets before it, its reals
+// ordered by the in-bin keys (r(b,s), s). For each requested bucket the call returns its output
+// offset and load, and appends the input indices of its reals in output order to `src`.
+// Returns OR_ERR_INVALID when `src` is too small. (No overflow check: callers sample runs that
+// reported no overflow.)
+int or_orp_sample(uint64_t n, uint32_t Z, uint64_t seed, uint32_t attempt, const uint64_t* buckets,
+                  uint32_t nb, uint64_t* offset, uint32_t* load, uint64_t* src, uint64_t cap) {
+  uint64_t B;
+  uint32_t L;
+  geometry(n, Z, &B, &L);
+  std::vector<uint32_t> labels(n);
+  std::vector<uint64_t> loads(B, 0);
+  for (uint64_t i = 0; i < n; ++i) {
+    labels[i] = label_of(i, seed, attempt, L);
+    loads[labels[i]]++;
+  }
+  std::vector<uint64_t> starts(B + 1, 0);
+  for (uint64_t b = 0; b < B; ++b) starts[b + 1] = starts[b] + loads[b];
+  // members of every sampled bucket, in input order (one scan)
+  std::vector<int64_t> which(B, -1);
+  for (uint32_t x = 0; x < nb; ++x) {
+    if (buckets[x] >= B) return OR_ERR_INVALID;
+    which[buckets[x]] = x;
+  }
+  std::vector<std::vector<uint64_t>> mem(nb);
+  for (uint64_t i = 0; i < n; ++i)
+    if (which[labels[i]] >= 0) mem[which[labels[i]]].push_back(i);
+  uint64_t pos = 0;
+  for (uint32_t x = 0; x < nb; ++x) {
+    const uint64_t b = buckets[x];
+    offset[x] = starts[b];
+    load[x] = (uint32_t)loads[b];
+    const std::vector<uint64_t>& members = mem[which[b]];
+    const uint32_t m = (uint32_t)members.size();
+    std::vector<std::pair<uint64_t, uint32_t>> keyed(m);
+    for (uint32_t s = 0; s < m; ++s) {
+      uint32_t w[4];
+      philox_at(b * Z + s, attempt, 1, seed, w);
+      keyed[s] = {((uint64_t)w[0] << 32) | w[1], s};
+    }
+    std::sort(keyed.begin(), keyed.end());
+    if (pos + m > cap) return OR_ERR_INVALID;
+    for (uint32_t j = 0; j < m; ++j) src[pos + j] = members[keyed[j].second];
+    pos += m;
+  }
+  return OR_OK;
+}
+
 // ORP of one small array under `count` consecutive seeds; out receives count * n records.
 int or_orp_many(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t Z,
                 uint64_t seed0, uint64_t count, uint32_t max_attempts, int method,

@@ -345,3 +345,17 @@ def test_bitonic_network(n):
         np.testing.assert_array_equal(got, np.sort(r, order=["key", "payload"]))
     with pytest.raises(oracle.OracleError):
         oracle.bitonic_sort(inputs.make_records(12, 8))
+
+
+def test_orp_sample_equals_full_orp():
+    # The sampled form (bucket by bucket, any n) agrees with the full literal ORP on every bucket.
+    n, Z, seed = 20000, 64, 13
+    recs = inputs.make_records(n, 8, "uniform", seed=2)
+    out, info, loads = oracle.orp(recs, Z, seed, want_loads=True)
+    assert info.attempts == 1
+    buckets = np.arange(info.B)
+    off, load, src = oracle.orp_sample(n, Z, seed, buckets)
+    np.testing.assert_array_equal(load, loads)
+    for b in buckets:
+        seg = out["payload"][int(off[b]):int(off[b]) + int(load[b])]
+        np.testing.assert_array_equal(seg, src[b])
