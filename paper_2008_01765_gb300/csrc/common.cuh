@@ -93,6 +93,20 @@ template <> struct RecT<16> {
   __device__ __forceinline__ static T zero() { return make_uint4(0, 0, 0, 0); }
 };
 
+// Lanes of the warp whose value equals this lane's in the low nbits bits: one ballot per bit.
+// Measured on this part: cheaper than the match instruction when a warp holds many distinct
+// values (8-bit radix digits), dearer when it holds few (the butterfly's 2^k routing digits).
+__device__ __forceinline__ uint32_t ballot_peers(uint32_t v, uint32_t nbits) {
+  uint32_t peers = 0xFFFFFFFFu;
+#pragma unroll 4
+  for (uint32_t b = 0; b < nbits; ++b) {
+    const uint32_t bit = (v >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -124,6 +124,7 @@ constexpr int kMiscBar = 0;     // mbarrier (8 bytes)
 constexpr int kMiscNext = 2;    // next subproblem (u64 in words 2..3)
 constexpr int kMiscPrefix = 4;  // LAST: subproblem output prefix (u64 in words 4..5)
 constexpr int kMiscBefore = 8;  // LAST: reals of the lower-ranked CTAs of the subproblem
+constexpr int kMiscTotal = 10;  // LAST: reals of the subproblem (u64 in words 10..11)
 
 template <int R, int MODE, bool CL, bool TRACE>
 __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C) {
@@ -382,25 +383,14 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
     for (uint32_t x = tid; x < Dc * D; x += kT) h[x] = 0;  // read above; next use after a barrier
 
     if constexpr (LAST) {
-      // ---- decoupled look-back of the subproblem's output offset (rank 0, one thread) ----
+      // ---- publish this subproblem's reals (rank 0, one thread): the look-back that gives its
+      // output offset runs after the routing, when the predecessors have had time to finish ----
       if (crank == 0 && tid == kT - 32) {
         unsigned long long total = 0;
         for (uint32_t u = 0; u < D; ++u) total += min(tot[u], Z);
-        unsigned long long prefix = 0;
         const bool skip = a.skip_publish && q == 0;
-        if (q == 0) {
-          if (!skip) st_status(a.status, st_word(kStIncl, 0, total));
-        } else {
-          st_status(a.status + q, st_word(kStAgg, 0, total));
-          prefix = lookback_window<8>(a.status, q, 1, 0, a.ctrl);
-          st_status(a.status + q, st_word(kStIncl, 0, prefix + total));
-        }
-        if constexpr (CL) {
-          const uint32_t local = smem_u32(misc + kMiscPrefix);
-          for (uint32_t c = 0; c < C; ++c) st_cluster_u64(mapa(local, c), prefix);
-        } else {
-          *reinterpret_cast<unsigned long long*>(misc + kMiscPrefix) = prefix;
-        }
+        if (!skip) st_status(a.status + q, st_word(q == 0 ? kStIncl : kStAgg, 0, total));
+        *reinterpret_cast<unsigned long long*>(misc + kMiscTotal) = total;
       }
       // ---- in-bin permutation (Section 3.2) of own final buckets, built in the empty tile ----
       // Final bucket b = q*2^k + u holds m = min(tot[u], Z) reals at stable slots s < m; slot s
@@ -509,6 +499,23 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
             }
           }
           __syncwarp();
+        }
+      }
+    }
+    if constexpr (LAST) {
+      // ---- decoupled look-back of the subproblem's output offset (rank 0, one thread) ----
+      if (crank == 0 && tid == kT - 32) {
+        unsigned long long prefix = 0;
+        if (q > 0) {
+          const unsigned long long total = *reinterpret_cast<unsigned long long*>(misc + kMiscTotal);
+          prefix = lookback_window<8>(a.status, q, 1, 0, a.ctrl);
+          st_status(a.status + q, st_word(kStIncl, 0, prefix + total));
+        }
+        if constexpr (CL) {
+          const uint32_t local = smem_u32(misc + kMiscPrefix);
+          for (uint32_t c = 0; c < C; ++c) st_cluster_u64(mapa(local, c), prefix);
+        } else {
+          *reinterpret_cast<unsigned long long*>(misc + kMiscPrefix) = prefix;
         }
       }
     }
