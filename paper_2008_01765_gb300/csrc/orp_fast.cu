@@ -119,6 +119,15 @@ __host__ __device__ inline FastLayout fast_layout(int R, uint32_t Z, uint32_t k,
   return l;
 }
 
+// In-bin permutation tie-break for two slots of one final bucket (base = b*Z) whose keys agree
+// in word 0: slot s3 sorts before slot s2 iff its word 1 is smaller, or equal with s3 < s2.
+// Rare (equal 32-bit words), so kept out of line.
+__device__ __noinline__ bool perm_tie_less(uint64_t base, uint32_t s3, uint32_t s2, uint32_t attempt, uint64_t seed) {
+  const uint32_t l2 = philox_at(base + s2, attempt, 1, seed).w1;
+  const uint32_t l3 = philox_at(base + s3, attempt, 1, seed).w1;
+  return (l3 < l2) || (l3 == l2 && s3 < s2);
+}
+
 // misc words
 constexpr int kMiscBar = 0;     // mbarrier (8 bytes)
 constexpr int kMiscNext = 2;    // next subproblem (u64 in words 2..3)
@@ -395,27 +404,47 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
       // ---- in-bin permutation (Section 3.2) of own final buckets, built in the empty tile ----
       // Final bucket b = q*2^k + u holds m = min(tot[u], Z) reals at stable slots s < m; slot s
       // gets the key r = (w0 << 32 | w1) of Philox(b*Z + s, attempt, stream 1) and the reals are
-      // ordered by (r, s). All warps rank all own buckets at once: count the top 8 bits of w0 per
-      // bucket, scan, list each bin's members, and rank a slot among its bin's members by
-      // (w0, w1, s). inv[up*Z + rank] = s.
+      // ordered by (r, s). The CTA's reals are numbered y = moff[up] + s across its own buckets
+      // and every step runs over all of them at once: count the top 8 bits of w0 per bucket,
+      // scan, list each bin's members, and rank a real among its bin's members by (w0, w1, s).
+      // inv[up*Z + rank] = s.
       {
-        uint32_t* rhi = reinterpret_cast<uint32_t*>(smem + lay.perm);
-        uint32_t* bstart = rhi + S;
-        uint32_t* bcur = bstart + Dc * 256;
-        uint16_t* members = reinterpret_cast<uint16_t*>(bcur + Dc * 256);
+        uint32_t* rhi = reinterpret_cast<uint32_t*>(smem + lay.perm);      // [S] w0 by real index
+        uint32_t* bstart = rhi + S;                                        // [Dc][256]
+        uint32_t* bcur = bstart + Dc * 256;                                // [Dc][256]
+        uint16_t* members = reinterpret_cast<uint16_t*>(bcur + Dc * 256);  // [S] real indexes by bin
         for (uint32_t x = tid; x < Dc * 256; x += kT) bcur[x] = 0;
+        if (tid == 0) {
+          uint32_t run = 0;
+          for (uint32_t up = 0; up < Dc; ++up) {
+            moff[up] = run;
+            run += min(tot[crank * Dc + up], Z);
+          }
+          moff[Dc] = run;
+        }
         __syncthreads();
-        for (uint32_t up = 0; up < Dc; ++up) {
-          const uint32_t m = min(tot[crank * Dc + up], Z);
-          const uint64_t b = q * D + crank * Dc + up;
-          for (uint32_t s2 = tid; s2 < m; s2 += kT) {
-            const uint32_t hh = philox_at(b * Z + s2, a.attempt, 1, a.seed).w0;
-            rhi[up * Z + s2] = hh;
+        const uint32_t M = moff[Dc];
+        const uint64_t b0 = q * D + crank * Dc;
+        {
+          uint32_t up = 0, up2 = 0;
+          for (uint32_t y = tid; y < M; y += 2 * kT) {  // two independent Philox chains per step
+            const uint32_t y2 = y + kT;
+            while (moff[up + 1] <= y) ++up;
+            up2 = up2 < up ? up : up2;
+            if (y2 < M)
+              while (moff[up2 + 1] <= y2) ++up2;
+            const uint32_t hh = philox_at((b0 + up) * Z + (y - moff[up]), a.attempt, 1, a.seed).w0;
+            const uint32_t hh2 = philox_at((b0 + up2) * Z + (y2 - moff[up2]), a.attempt, 1, a.seed).w0;
+            rhi[y] = hh;
             atomicAdd(&bcur[up * 256 + (hh >> 24)], 1u);
+            if (y2 < M) {
+              rhi[y2] = hh2;
+              atomicAdd(&bcur[up2 * 256 + (hh2 >> 24)], 1u);
+            }
           }
         }
         __syncthreads();
-        for (uint32_t up = warp; up < Dc; up += kW) {  // segmented exclusive scan, one warp per bucket
+        for (uint32_t up = warp; up < Dc; up += kW) {  // exclusive scan per bucket, one warp each
           uint32_t v[8], sum = 0;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -428,7 +457,7 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
             if (lane >= o) incl += y;
           }
-          uint32_t run = incl - sum;
+          uint32_t run = moff[up] + incl - sum;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             bstart[up * 256 + lane * 8 + e] = run;
@@ -437,31 +466,27 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
           }
         }
         __syncthreads();
-        for (uint32_t up = 0; up < Dc; ++up) {
-          const uint32_t m = min(tot[crank * Dc + up], Z);
-          for (uint32_t s2 = tid; s2 < m; s2 += kT)
-            members[up * Z + atomicAdd(&bcur[up * 256 + (rhi[up * Z + s2] >> 24)], 1u)] = (uint16_t)s2;
+        {
+          uint32_t up = 0;
+          for (uint32_t y = tid; y < M; y += kT) {
+            while (moff[up + 1] <= y) ++up;
+            members[atomicAdd(&bcur[up * 256 + (rhi[y] >> 24)], 1u)] = (uint16_t)y;
+          }
         }
         __syncthreads();
-        for (uint32_t up = 0; up < Dc; ++up) {
-          const uint32_t m = min(tot[crank * Dc + up], Z);
-          const uint64_t b = q * D + crank * Dc + up;
-          for (uint32_t s2 = tid; s2 < m; s2 += kT) {
-            const uint32_t hh = rhi[up * Z + s2], bin = up * 256 + (hh >> 24);
-            uint32_t r = bstart[bin];
+        {
+          uint32_t up = 0;
+          for (uint32_t y = tid; y < M; y += kT) {
+            while (moff[up + 1] <= y) ++up;
+            const uint32_t hh = rhi[y], bin = up * 256 + (hh >> 24), mo = moff[up];
+            uint32_t r = bstart[bin] - mo;
             for (uint32_t x = bstart[bin], e = bcur[bin]; x < e; ++x) {
-              const uint32_t s3 = members[up * Z + x];
-              if (s3 == s2) continue;
-              const uint32_t h3 = rhi[up * Z + s3];
-              bool less = h3 < hh;
-              if (h3 == hh) {  // equal high words: compare the low words, then the slot
-                const uint32_t l1 = philox_at(b * Z + s2, a.attempt, 1, a.seed).w1;
-                const uint32_t l3 = philox_at(b * Z + s3, a.attempt, 1, a.seed).w1;
-                less = (l3 < l1) || (l3 == l1 && s3 < s2);
-              }
-              r += less;
+              const uint32_t y3 = members[x];
+              if (y3 == y) continue;
+              const uint32_t h3 = rhi[y3];
+              r += (h3 < hh) || (h3 == hh && perm_tie_less((b0 + up) * Z, y3 - mo, y - mo, a.attempt, a.seed));
             }
-            inv[up * Z + r] = (uint16_t)s2;
+            inv[up * Z + r] = (uint16_t)(y - mo);
           }
         }
       }
