@@ -178,7 +178,8 @@ bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t 
  * {(kind << 56) | (buffer << 48) | bytes, byte offset within that buffer}; word 0 of d_buf
  * counts the entries written (entries beyond the buffer's capacity are counted, not stored).
  * kind: 1 = read, 2 = write. buffer: 0 = input, 1 = slot records A, 2 = slot tags A,
- * 3 = slot records B, 4 = slot tags B, 5 = output. Attach NULL to detach. The trace run uses
+ * 3 = slot records B, 4 = slot tags B, 5 = output, 6 = sort scratch in the workspace,
+ * 7 = in-bin permutation table in the workspace. Attach NULL to detach. The trace run uses
  * separate kernel instances; the results are identical. */
 bos_status bos_trace_attach(void* d_buf, size_t bytes);
 

@@ -18,10 +18,10 @@ constexpr uint32_t kDefaultAttempts = 8;
 Trace g_trace{nullptr, 0};
 
 // ---- opt-in kernel timing (bos_profile_enable / bos_profile_read) ----
-enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKCount };
+enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKPerm, kKCount };
 const char* const kKNames[kKCount] = {"orp_pass_first", "orp_pass_mid", "orp_pass_last", "orp_pass_single",
                                      "radix_hist", "radix_prep", "radix_pass", "radix_pass_skipped",
-                                     "bitonic"};
+                                     "bitonic", "perm_table"};
 constexpr int kMaxEv = 1024;
 struct Prof {
   bool on = false;
@@ -78,7 +78,7 @@ struct Plan {
   uint32_t pass_C[kMaxPasses] = {};
   // workspace offsets
   size_t off_ctrl = 0, off_rec[2] = {0, 0}, off_tag[2] = {0, 0}, off_status = 0;
-  size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, total = 0;
+  size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, off_ord = 0, total = 0;
   uint64_t orp_tiles = 0, radix_tiles = 0;
 };
 
@@ -265,6 +265,7 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
     pl->off_tag[x] = off; off = align256(off + slots * 4);
   }
   pl->orp_tiles = B >> pl->pass_k[pl->npass - 1];
+  pl->off_ord = off; off = align256(off + slots * 2);  // in-bin permutation table (u16 per slot)
   // sized for the largest last pass (k = 1) so the workspace does not depend on k
   pl->off_status = off; off = align256(off + B * 8);
   if (sort) {
@@ -415,6 +416,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         a.out_sel = sort ? 1u : 0u;
         a.status = (unsigned long long*)(ws + pl.off_status);
         a.skip_publish = (p->flags & BOS_FLAG_SKIP_PUBLISH) ? 1u : 0u;
+        a.ord = (const uint16_t*)(ws + pl.off_ord);
       }
       a.n = n;
       a.B = pl.B;
@@ -430,9 +432,27 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       const int mode = (first ? kModeFirst : 0) | (last ? kModeLast : 0);
       // algorithmic bytes: whole slot arrays in and out, the input and output records once
       const double slot_bytes = (double)pl.B * pl.Z * (pl.R + 4);
-      const double in_b = first ? (double)n * pl.R : slot_bytes;
+      const double in_b = (first ? (double)n * pl.R : slot_bytes) + (last && pl.fast ? (double)pl.B * pl.Z * 2 : 0.0);
       const double out_b = last ? (double)n * pl.R : slot_bytes;
       const int cls = first && last ? kKSingle : first ? kKFirst : last ? kKLast : kKMid;
+      if (last && pl.fast) {  // the LAST pass's in-bin permutation table for this attempt
+        PermTableArgs ta{};
+        ta.ord = (uint16_t*)(ws + pl.off_ord);
+        ta.tag = first ? nullptr : a.in_tag;  // a single pass has no input tags: rows of all Z slots
+        ta.B = pl.B;
+        ta.Z = pl.Z;
+        ta.attempt = attempt;
+        ta.i = a.i;
+        ta.k = a.k;
+        ta.L = pl.L;
+        ta.buf_tag = a.buf_in_tag;
+        ta.seed = p->seed;
+        ta.trace = g_trace;
+        const double tb = (double)pl.B * pl.Z * (2.0 + (first ? 0.0 : 4.0));  // rows out, tags in
+        const int evt = prof_begin(st, kKPerm, tb);
+        BOS_CUDA(launch_perm_table(ta, st, trace));
+        prof_end(evt, st);
+      }
       const int ev = prof_begin(st, cls, in_b + out_b);
       if (pl.fast)
         BOS_CUDA(launch_orp_fast(a, mode, pl.pass_C[x], 0, st, pl.R, trace));

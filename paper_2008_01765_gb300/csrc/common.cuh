@@ -256,7 +256,8 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 // Debug address trace: {(kind << 56) | (buffer << 48) | bytes, byte offset}.
 // ---------------------------------------------------------------------------------------------
 enum TraceBuf : uint32_t {
-  kBufIn = 0, kBufRecA = 1, kBufTagA = 2, kBufRecB = 3, kBufTagB = 4, kBufOut = 5, kBufTmp = 6
+  kBufIn = 0, kBufRecA = 1, kBufTagA = 2, kBufRecB = 3, kBufTagB = 4, kBufOut = 5, kBufTmp = 6,
+  kBufPerm = 7
 };
 enum TraceKind : uint32_t { kRead = 1, kWrite = 2 };
 

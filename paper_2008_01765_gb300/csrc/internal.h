@@ -29,7 +29,22 @@ struct PassArgs {
   unsigned long long* status;  // LAST: look-back words, one per subproblem
   uint32_t buf_in_rec, buf_in_tag, buf_out_rec, buf_out_tag;  // trace buffer ids
   Trace trace;
+  const uint16_t* ord;      // LAST (persistent kernel): in-bin permutation table, B*Z slot indexes
 };
+
+// In-bin permutation table (perm_table.cu): row b < B lists final bucket b's slots in the order
+// of the Section 3.2 keys of (b, attempt, seed), ord[b*Z + rank] = slot. With the LAST pass's
+// input tags (tag != null; levels i..i+k-1 of L) a row holds the bucket's m real slots, then
+// 0xFFFF; without them, all Z slots. Z a multiple of 32, <= 4096; k <= 12.
+struct PermTableArgs {
+  uint16_t* ord;
+  const uint32_t* tag;
+  uint64_t B;
+  uint32_t Z, attempt, i, k, L, buf_tag;
+  uint64_t seed;
+  Trace trace;
+};
+cudaError_t launch_perm_table(const PermTableArgs& a, cudaStream_t st, bool trace);
 
 uint32_t orp_smem_bytes(int R, uint32_t Z, uint32_t k, bool last);
 

@@ -104,28 +104,16 @@ __host__ __device__ inline FastLayout fast_layout(int R, uint32_t Z, uint32_t k,
   l.tot = off;      off = fl_align(off + D * 4, 16);
   l.moff = off;     off = fl_align(off + (Dc + 1) * 4, 16);
   l.misc = off;     off = fl_align(off + 128, 16);
-  // LAST: in-bin permutation scratch = Dc*Z key words, Dc x 256 bin starts and cursors, Dc*Z
-  // member slots (u16). It lives in the (still empty) record tile when it fits there.
+  // LAST: the CTA's rows of the in-bin permutation table (u16 per slot) use the tag tile; the
+  // filter keeps one count per 32 table entries and one partial sum per warp.
   l.perm_bytes = 0;
-  l.perm = l.tile_rec;
+  l.perm = off;
   if (last) {
-    l.perm_bytes = S * 4 + Dc * 256 * 4 * 2 + S * 2;
-    if (S * R < l.perm_bytes) {
-      l.perm = off;
-      off = fl_align(off + l.perm_bytes, 16);
-    }
+    l.perm_bytes = (S / 32 + kW) * 4;
+    off = fl_align(off + l.perm_bytes, 16);
   }
   l.total = off;
   return l;
-}
-
-// In-bin permutation tie-break for two slots of one final bucket (base = b*Z) whose keys agree
-// in word 0: slot s3 sorts before slot s2 iff its word 1 is smaller, or equal with s3 < s2.
-// Rare (equal 32-bit words), so kept out of line.
-__device__ __noinline__ bool perm_tie_less(uint64_t base, uint32_t s3, uint32_t s2, uint32_t attempt, uint64_t seed) {
-  const uint32_t l2 = philox_at(base + s2, attempt, 1, seed).w1;
-  const uint32_t l3 = philox_at(base + s3, attempt, 1, seed).w1;
-  return (l3 < l2) || (l3 == l2 && s3 < s2);
 }
 
 // misc words
@@ -134,6 +122,7 @@ constexpr int kMiscNext = 2;    // next subproblem (u64 in words 2..3)
 constexpr int kMiscPrefix = 4;  // LAST: subproblem output prefix (u64 in words 4..5)
 constexpr int kMiscBefore = 8;  // LAST: reals of the lower-ranked CTAs of the subproblem
 constexpr int kMiscTotal = 10;  // LAST: reals of the subproblem (u64 in words 10..11)
+constexpr int kMiscBarOrd = 12;  // LAST: mbarrier of the permutation table rows (8 bytes)
 
 template <int R, int MODE, bool CL, bool TRACE>
 __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C) {
@@ -147,15 +136,15 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
   const FastLayout lay = fast_layout(R, Z, k, C, LAST);
   Rec* tile_rec = reinterpret_cast<Rec*>(smem + lay.tile_rec);
   uint32_t* tile_tag = reinterpret_cast<uint32_t*>(smem + lay.tile_tag);
-  uint16_t* inv = reinterpret_cast<uint16_t*>(smem + lay.tile_tag);
+  uint16_t* ordl = reinterpret_cast<uint16_t*>(smem + lay.tile_tag);  // LAST: own table rows
   uint32_t* tags = reinterpret_cast<uint32_t*>(smem + lay.tags);
   uint32_t* rc = reinterpret_cast<uint32_t*>(smem + lay.rc);      // [kW][D]
   uint32_t* h = reinterpret_cast<uint32_t*>(smem + lay.h);        // [Dc][D]
   uint32_t* aggs = reinterpret_cast<uint32_t*>(smem + lay.aggs);  // [C][D]
   uint32_t* tot = reinterpret_cast<uint32_t*>(smem + lay.tot);    // [D]
-  uint32_t* moff = reinterpret_cast<uint32_t*>(smem + lay.moff);  // [Dc+1]
   uint32_t* misc = reinterpret_cast<uint32_t*>(smem + lay.misc);
   const uint32_t bar = smem_u32(misc + kMiscBar);
+  const uint32_t bar_ord = smem_u32(misc + kMiscBarOrd);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = lanemask_lt();
@@ -175,6 +164,7 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
   // ---- set-up ----
   if (tid == 0) {
     mbar_init(bar, 1);
+    if constexpr (LAST) mbar_init(bar_ord, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (uint32_t x = tid; x < kW * D; x += kT) rc[x] = 0;
@@ -198,7 +188,7 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
   if constexpr (CL) cluster_sync();
 
   uint64_t q = *reinterpret_cast<unsigned long long*>(misc + kMiscNext);
-  uint32_t parity = 0;
+  uint32_t parity = 0, parity_ord = 0;
 
   // input bucket (global index) of own input bucket s' of subproblem qq
   auto in_bucket = [&](uint64_t qq, uint32_t sp) -> uint64_t {
@@ -264,6 +254,16 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
   issue_tags(q);
 
   while (q < nsub) {
+    if constexpr (LAST) {
+      // the table rows of own final buckets q*2^k + crank*Dc + up, up < Dc: one contiguous run
+      // (the tag tile is free: the previous subproblem's filter ended with a barrier)
+      if (tid == 0) {
+        const uint64_t first = (q * D + crank * Dc) * (uint64_t)Z;
+        mbar_expect_tx(bar_ord, S * 2);
+        tma_load(smem_u32(ordl), a.ord + first, S * 2, bar_ord);
+        trace_log<TRACE>(a.trace, kRead, kBufPerm, S * 2, first * 2);
+      }
+    }
     load_rows(q, 0, rows0, rr);
     // FIRST: labels into the tag stage; later passes: wait for the tags' TMA
     if constexpr (FIRST) {
@@ -401,99 +401,6 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
         if (!skip) st_status(a.status + q, st_word(q == 0 ? kStIncl : kStAgg, 0, total));
         *reinterpret_cast<unsigned long long*>(misc + kMiscTotal) = total;
       }
-      // ---- in-bin permutation (Section 3.2) of own final buckets, built in the empty tile ----
-      // Final bucket b = q*2^k + u holds m = min(tot[u], Z) reals at stable slots s < m; slot s
-      // gets the key r = (w0 << 32 | w1) of Philox(b*Z + s, attempt, stream 1) and the reals are
-      // ordered by (r, s). The CTA's reals are numbered y = moff[up] + s across its own buckets
-      // and every step runs over all of them at once: count the top 8 bits of w0 per bucket,
-      // scan, list each bin's members, and rank a real among its bin's members by (w0, w1, s).
-      // inv[up*Z + rank] = s.
-      {
-        uint32_t* rhi = reinterpret_cast<uint32_t*>(smem + lay.perm);      // [S] w0 by real index
-        uint32_t* bstart = rhi + S;                                        // [Dc][256]
-        uint32_t* bcur = bstart + Dc * 256;                                // [Dc][256]
-        uint16_t* members = reinterpret_cast<uint16_t*>(bcur + Dc * 256);  // [S] real indexes by bin
-        for (uint32_t x = tid; x < Dc * 256; x += kT) bcur[x] = 0;
-        if (tid == 0) {
-          uint32_t run = 0;
-          for (uint32_t up = 0; up < Dc; ++up) {
-            moff[up] = run;
-            run += min(tot[crank * Dc + up], Z);
-          }
-          moff[Dc] = run;
-        }
-        __syncthreads();
-        const uint32_t M = moff[Dc];
-        const uint64_t b0 = q * D + crank * Dc;
-        {
-          uint32_t up = 0, up2 = 0;
-          for (uint32_t y = tid; y < M; y += 2 * kT) {  // two independent Philox chains per step
-            const uint32_t y2 = y + kT;
-            while (moff[up + 1] <= y) ++up;
-            up2 = up2 < up ? up : up2;
-            if (y2 < M)
-              while (moff[up2 + 1] <= y2) ++up2;
-            const uint32_t hh = philox_at((b0 + up) * Z + (y - moff[up]), a.attempt, 1, a.seed).w0;
-            const uint32_t hh2 = philox_at((b0 + up2) * Z + (y2 - moff[up2]), a.attempt, 1, a.seed).w0;
-            rhi[y] = hh;
-            atomicAdd(&bcur[up * 256 + (hh >> 24)], 1u);
-            if (y2 < M) {
-              rhi[y2] = hh2;
-              atomicAdd(&bcur[up2 * 256 + (hh2 >> 24)], 1u);
-            }
-          }
-        }
-        __syncthreads();
-        for (uint32_t up = warp; up < Dc; up += kW) {  // exclusive scan per bucket, one warp each
-          uint32_t v[8], sum = 0;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            v[e] = bcur[up * 256 + lane * 8 + e];
-            sum += v[e];
-          }
-          uint32_t incl = sum;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          uint32_t run = moff[up] + incl - sum;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            bstart[up * 256 + lane * 8 + e] = run;
-            bcur[up * 256 + lane * 8 + e] = run;
-            run += v[e];
-          }
-        }
-        __syncthreads();
-        {
-          uint32_t up = 0;
-          for (uint32_t y = tid; y < M; y += kT) {
-            while (moff[up + 1] <= y) ++up;
-            members[atomicAdd(&bcur[up * 256 + (rhi[y] >> 24)], 1u)] = (uint16_t)y;
-          }
-        }
-        __syncthreads();
-        {
-          uint32_t up = 0;
-          for (uint32_t y = tid; y < M; y += kT) {
-            while (moff[up + 1] <= y) ++up;
-            const uint32_t hh = rhi[y], bin = up * 256 + (hh >> 24), mo = moff[up];
-            uint32_t r = bstart[bin] - mo;
-            for (uint32_t x = bstart[bin], e = bcur[bin]; x < e; ++x) {
-              const uint32_t y3 = members[x];
-              if (y3 == y) continue;
-              const uint32_t h3 = rhi[y3];
-              r += (h3 < hh) || (h3 == hh && perm_tie_less((b0 + up) * Z, y3 - mo, y - mo, a.attempt, a.seed));
-            }
-            inv[up * Z + r] = (uint16_t)(y - mo);
-          }
-        }
-      }
-      if constexpr (CL)
-        cluster_sync();  // scratch use of every tile ends before anyone routes into it
-      else
-        __syncthreads();
     }
 
     // ---- phase 3: route every real to its output slot (own tile or a peer's tile) ----
@@ -590,36 +497,62 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
       }
     } else {
       // ---- LAST: write own reals compacted, in permuted order ----
+      // Bucket up's reals sit at slots s < m = min(tot, Z); its table row lists all Z slots in key
+      // order, so its output is the row with the entries >= m dropped. Every 32 entries give one
+      // ballot; an exclusive scan of the ballot counts over the CTA's rows places them.
       if (tid == 0) {
         uint32_t before = 0;  // reals of lower-ranked CTAs of this subproblem
         for (uint32_t u = 0; u < crank * Dc; ++u) before += min(tot[u], Z);
-        uint32_t run = 0;
-        for (uint32_t up = 0; up < Dc; ++up) {
-          moff[up] = run;
-          run += min(tot[crank * Dc + up], Z);
-        }
-        moff[Dc] = run;
         misc[kMiscBefore] = before;
+      }
+      uint32_t* ccnt = reinterpret_cast<uint32_t*>(smem + lay.perm);  // [S/32]
+      uint32_t* cw = ccnt + S / 32;                                     // [kW]
+      const uint32_t cpb = Z >> 5, nch = S >> 5;                        // chunks per bucket, in all
+      mbar_wait(bar_ord, parity_ord, a.ctrl);
+      parity_ord ^= 1u;
+      for (uint32_t c = warp; c < nch; c += kW) {
+        const uint32_t up = c / cpb, m = min(tot[crank * Dc + up], Z);
+        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, ordl[c * 32 + lane] < m);
+        if (lane == 0) ccnt[c] = __popc(keep);
+      }
+      __syncthreads();
+      {  // exclusive scan of ccnt: thread t takes chunks [t*per, (t+1)*per)
+        const uint32_t per = (nch + kT - 1) / kT, c0 = tid * per, c1 = min(c0 + per, nch);
+        uint32_t sum = 0;
+        for (uint32_t c = c0; c < c1; ++c) sum += ccnt[c];
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (lane == 31) cw[warp] = incl;
+        __syncthreads();
+        uint32_t run = incl - sum;
+        for (int w = 0; w < warp; ++w) run += cw[w];
+        for (uint32_t c = c0; c < c1; ++c) {
+          const uint32_t x = ccnt[c];
+          ccnt[c] = run;
+          run += x;
+        }
       }
       __syncthreads();
       const uint64_t gofs = *reinterpret_cast<unsigned long long*>(misc + kMiscPrefix) + misc[kMiscBefore];
-      const uint32_t total = moff[Dc];
       Rec* out = reinterpret_cast<Rec*>(a.out0);
       if (a.out_sel && (__popc(a.ctrl->radix_live) & 1)) out = reinterpret_cast<Rec*>(a.out1);
       const uint32_t out_buf = (out == reinterpret_cast<Rec*>(a.out0)) ? kBufOut : kBufTmp;
-      for (uint32_t j = tid; j < total; j += kT) {
-        uint32_t lo = 0, hi = Dc;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (moff[mid] <= j) lo = mid; else hi = mid;
-        }
-        const uint32_t s = inv[lo * Z + (j - moff[lo])];
-        if (gofs + j < a.n) {
-          out[gofs + j] = tile_rec[lo * Z + s];
-          trace_log<TRACE>(a.trace, kWrite, out_buf, R, (gofs + j) * R);
+      for (uint32_t c = warp; c < nch; c += kW) {
+        const uint32_t up = c / cpb, m = min(tot[crank * Dc + up], Z);
+        const uint32_t s = ordl[c * 32 + lane];
+        const bool real = s < m;
+        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, real);
+        const uint64_t pos = gofs + ccnt[c] + __popc(keep & lt_mask);
+        if (real && pos < a.n) {
+          out[pos] = tile_rec[up * Z + s];
+          trace_log<TRACE>(a.trace, kWrite, out_buf, R, pos * R);
         }
       }
-      __syncthreads();  // tile and inverse permutations are reused by the next subproblem
+      __syncthreads();  // the tile, the table rows and the counts are reused by the next subproblem
     }
     q = qnext;
   }
