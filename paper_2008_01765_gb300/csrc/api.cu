@@ -13,6 +13,7 @@ namespace {
 constexpr uint32_t kMaxSmem = 232448 - 1024;  // opt-in shared memory per CTA (sm_100/103) less static use
 constexpr uint32_t kMaxK = 6;          // per-pass digit-count table is (2^k)^2 words
 constexpr uint32_t kMaxPasses = 32;
+constexpr uint32_t kMaxLevels = 32;  // L < 32: slot indexes are 32-bit
 constexpr uint32_t kDefaultAttempts = 8;
 
 Trace g_trace{nullptr, 0};
@@ -192,61 +193,85 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
       pl->pass_C[x] = C;
     }
   } else {
-    // Cost model from GB300 measurements of the persistent kernel (time per slot of a butterfly
-    // pass relative to the cluster-free kernel): a cluster applies more levels per pass but its
-    // two cluster barriers per subproblem slow each pass. The first and the last pass (which
-    // also draw labels or build the in-bin permutations) run without clusters; the middle levels
-    // take the cluster size with the lowest total cost. Ties go to fewer passes.
-    static const double kRel[5] = {1.0, 1.09, 1.37, 1.63, 2.46};  // C = 1, 2, 4, 8, 16
-    uint32_t kf = max_k_fast(pl->R, p->Z, 1, false), kl = max_k_fast(pl->R, p->Z, 1, true);
-    uint32_t ks = kl;  // single FIRST+LAST pass
-    if (p->k) {
-      kf = kf < p->k ? kf : p->k;
-      kl = kl < p->k ? kl : p->k;
-      ks = ks < p->k ? ks : p->k;
-    }
-    if (kf == 0 || kl == 0) return BOS_ERR_INVALID;  // (checked above)
+    // Cost model from GB300 measurements of the persistent kernel: the time of one pass by role
+    // and cluster size C, relative to a cluster-free middle pass (n = 2^30 16-byte records,
+    // Z = 1024; each pass applying the most levels its C holds: 3, 4, 5, 6, 7). A cluster applies
+    // more levels per pass, but its cluster barriers slow each subproblem; the first pass also
+    // draws labels, the last one also writes the compacted output. Each pass takes the smallest
+    // C that holds its levels; the first and last pass sizes are enumerated and the middle levels
+    // split by dynamic programming. Ties go to fewer passes.
+    static const double kMid[5] = {1.0, 1.371, 1.623, 1.919, 2.49};  // C = 1, 2, 4, 8, 16
+    static const double kFirst[5] = {1.269, 1.496, 1.667, 2.168, 2.63};
+    static const double kLast[5] = {1.219, 1.459, 1.723, 2.212, 2.63};
+    const uint32_t kcap = p->k ? p->k : kMaxKFast;
+    auto c_for = [&](uint32_t k, bool last) -> uint32_t {  // smallest C holding k levels; 0: none
+      if (k > kcap) return 0;
+      for (uint32_t C = 1; C <= max_C; C <<= 1)
+        if ((1u << k) >= C && k <= max_k_fast(pl->R, p->Z, C, last)) return C;
+      return 0;
+    };
+    auto ci = [](uint32_t C) { return (uint32_t)__builtin_ctz(C); };
+    uint32_t ks = max_k_fast(pl->R, p->Z, 1, true);  // single FIRST+LAST pass (no cluster)
+    if (p->k) ks = ks < p->k ? ks : p->k;
+    if (ks == 0) return BOS_ERR_INVALID;  // (checked above)
     if (L <= ks) {
       pl->npass = 1;
       pl->pass_k[0] = L;
       pl->pass_C[0] = 1;
     } else {
-      double best = 1e30;
-      uint32_t best_f = 0, best_l = 0, best_C = 1, best_m = 0;
-      for (uint32_t f = 1; f <= kf && f < L; ++f) {
-        for (uint32_t l = 1; l <= kl && f + l <= L; ++l) {
-          const uint32_t M = L - f - l;
-          for (uint32_t ci = 0, C = 1; C <= max_C; ++ci, C <<= 1) {
-            uint32_t km = max_k_fast(pl->R, p->Z, C, false);
-            if (p->k) km = km < p->k ? km : p->k;
-            if (M > 0 && km == 0) continue;
-            const uint32_t m = M ? (M + km - 1) / km : 0;
-            const double cost = 2.0 + m * (M ? kRel[ci] : 0.0) - 1e-3 * (f + l);
-            if (cost < best - 1e-9) {
-              best = cost;
-              best_f = f;
-              best_l = l;
-              best_C = C;
-              best_m = m;
-            }
-            if (!M) break;
+      // best[M]: cheapest split of M middle levels (cost, passes, first pass size)
+      double best[kMaxLevels + 1];
+      uint32_t npb[kMaxLevels + 1], take[kMaxLevels + 1];
+      best[0] = 0.0;
+      npb[0] = 0;
+      take[0] = 0;
+      for (uint32_t M = 1; M <= L; ++M) {
+        best[M] = 1e30;
+        npb[M] = 0;
+        take[M] = 0;
+        for (uint32_t k = 1; k <= M; ++k) {
+          const uint32_t C = c_for(k, false);
+          if (!C || best[M - k] >= 1e29) continue;
+          const double c = kMid[ci(C)] + best[M - k];
+          const uint32_t np = npb[M - k] + 1;
+          if (c < best[M] - 1e-9 || (c < best[M] + 1e-9 && np < npb[M])) {
+            best[M] = c;
+            npb[M] = np;
+            take[M] = k;
           }
         }
       }
-      if (best_f == 0 || 2 + best_m > kMaxPasses) return BOS_ERR_INVALID;
-      const uint32_t M = L - best_f - best_l;
-      pl->npass = 2 + best_m;
-      pl->pass_k[0] = best_f;
-      pl->pass_C[0] = 1;
-      for (uint32_t x = 0; x < best_m; ++x) {
-        pl->pass_k[1 + x] = M / best_m + (x < M % best_m);
-        uint32_t C = 1;  // smallest cluster that holds this pass's levels
-        while (C < best_C && (pl->pass_k[1 + x] > max_k_fast(pl->R, p->Z, C, false) || (1u << pl->pass_k[1 + x]) < C))
-          C <<= 1;
-        pl->pass_C[1 + x] = C;
+      double bc = 1e30;
+      uint32_t bf = 0, bl = 0, bnp = 0;
+      for (uint32_t f = 1; f < L; ++f) {
+        const uint32_t Cf = c_for(f, false);
+        if (!Cf) continue;
+        for (uint32_t l = 1; f + l <= L; ++l) {
+          const uint32_t Cl = c_for(l, true), M = L - f - l;
+          if (!Cl || best[M] >= 1e29 || 2 + npb[M] > kMaxPasses) continue;
+          const double c = kFirst[ci(Cf)] + kLast[ci(Cl)] + best[M];
+          const uint32_t np = 2 + npb[M];
+          if (c < bc - 1e-9 || (c < bc + 1e-9 && np < bnp)) {
+            bc = c;
+            bf = f;
+            bl = l;
+            bnp = np;
+          }
+        }
       }
-      pl->pass_k[pl->npass - 1] = best_l;
-      pl->pass_C[pl->npass - 1] = 1;
+      if (!bf) return BOS_ERR_INVALID;
+      pl->npass = bnp;
+      pl->pass_k[0] = bf;
+      pl->pass_C[0] = c_for(bf, false);
+      uint32_t M = L - bf - bl, x = 1;
+      while (M) {
+        pl->pass_k[x] = take[M];
+        pl->pass_C[x] = c_for(take[M], false);
+        M -= take[M];
+        ++x;
+      }
+      pl->pass_k[bnp - 1] = bl;
+      pl->pass_C[bnp - 1] = c_for(bl, true);
     }
   }
   uint32_t lvl = 0;
