@@ -138,22 +138,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def source_hash():
+def source_hash(files=None):
+    """Hash of the kernel sources (all of csrc/, or the named files of it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2008_01765_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    names = files if files else [f for f in sorted(os.listdir(csrc)) if f.endswith((".cu", ".cuh", ".h"))]
+    for f in names:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    """DRAM bytes per launch from the committed ncu summary, if the sources that define the kernel
+    (its entry's "sources", else all of csrc/) are the ones it was taken on."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t.get(workload, {}).get(kernel)
-        if e and e.get("source_hash") == source_hash():
+        if e and e.get("source_hash") == source_hash(e.get("sources")):
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
