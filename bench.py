@@ -522,6 +522,18 @@ def main():
         pms = e0.elapsed_time(e1) / 2
         comp["plain_k1"] = {"value": n / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
                             "orp_passes": int(pinfo.passes)}
+        # the comparison-based sort after the ORP (stable merge sort) in place of the radix sort
+        p.flags = args.flags | bos.FLAG_MERGE_SORT
+        step(3500)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(2):
+            step(1 + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p.flags = args.flags
+        mms = e0.elapsed_time(e1) / 2
+        comp["orp_merge_sort"] = {"value": n / (mms / 1e3), "unit": UNIT, "ms_per_step": mms}
         del ws
         torch.cuda.empty_cache()
         bos.bitonic_sort(x, REC, out=out)

@@ -66,6 +66,9 @@ typedef enum {
 #define BOS_FLAG_PLAN_ONLY 0x10u
 /* Plan the fewest passes (largest clusters) instead of the measured-cost plan; same result. */
 #define BOS_FLAG_FEWEST_PASSES 0x8u
+/* bos_sort: sort the ORP's output with a stable GPU merge sort (comparison-based, as Section 3.3
+ * composes the ORP with a comparison sort) instead of the LSD radix sort. Same result. */
+#define BOS_FLAG_MERGE_SORT 0x20u
 /* Largest thread-block cluster a pass may use (1, 2, 4, 8 or 16; 0 = the library's choice).
  * Tuning only: the result never depends on it. */
 #define BOS_FLAG_MAX_CLUSTER(c) (((uint32_t)(c) & 0x1Fu) << 16)

@@ -19,10 +19,11 @@ constexpr uint32_t kDefaultAttempts = 8;
 Trace g_trace{nullptr, 0};
 
 // ---- opt-in kernel timing (bos_profile_enable / bos_profile_read) ----
-enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKPerm, kKCount };
+enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKPerm,
+              kKMergeBlock, kKMerge, kKCount };
 const char* const kKNames[kKCount] = {"orp_pass_first", "orp_pass_mid", "orp_pass_last", "orp_pass_single",
                                      "radix_hist", "radix_prep", "radix_pass", "radix_pass_skipped",
-                                     "bitonic", "perm_table"};
+                                     "bitonic", "perm_table", "merge_block", "merge_pass"};
 constexpr int kMaxEv = 1024;
 struct Prof {
   bool on = false;
@@ -392,9 +393,16 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   const uint32_t max_attempts = p->max_attempts ? p->max_attempts : kDefaultAttempts;
   const uint32_t forced = (p->flags >> 8) & 0xFFu;
   const bool trace = g_trace.buf != nullptr;
+  // the comparison sort (stable merge) in place of the radix sort; its block-sorted runs start
+  // in the buffer that leaves the last merge pass's output in d_out
+  const bool merge = sort && (p->flags & BOS_FLAG_MERGE_SORT);
+  void* merge_first = merge ? ((merge_passes(n) & 1) ? (void*)(ws + pl.off_tmp) : d_out) : nullptr;
+  MergeHooks hooks{};
+  hooks.begin = [](cudaStream_t s2, int stage, double b) { return prof_begin(s2, stage ? kKMerge : kKMergeBlock, b); };
+  hooks.end = [](int slot, cudaStream_t s2) { prof_end(slot, s2); };
 
   RadixArgs ra{};
-  if (sort) {
+  if (sort && !merge) {
     ra.in = d_in;
     ra.buf0 = d_out;
     ra.buf1 = ws + pl.off_tmp;
@@ -409,7 +417,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   for (uint32_t attempt = 0; attempt < max_attempts; ++attempt) {
     BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
     BOS_CUDA(cudaMemsetAsync(ws + pl.off_status, 0, pl.orp_tiles * 8, st));
-    if (sort) {
+    if (sort && !merge) {
       BOS_CUDA(cudaMemsetAsync(ra.hist, 0, pl.digits * 256 * 4, st));
       BOS_CUDA(cudaMemsetAsync(ra.status, 0, pl.radix_tiles * 256 * 8, st));
       int ev = prof_begin(st, kKHist, (double)n * pl.key_bytes);
@@ -439,6 +447,10 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         a.out0 = d_out;
         a.out1 = sort ? ws + pl.off_tmp : d_out;
         a.out_sel = sort ? 1u : 0u;
+        if (merge) {
+          a.out0 = a.out1 = merge_first;
+          a.out_sel = 0u;
+        }
         a.status = (unsigned long long*)(ws + pl.off_status);
         a.skip_publish = (p->flags & BOS_FLAG_SKIP_PUBLISH) ? 1u : 0u;
         a.ord = (const uint16_t*)(ws + pl.off_ord);
@@ -485,7 +497,10 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         BOS_CUDA(launch_orp_pass(a, mode, pl.B >> a.k, st, pl.R, trace));
       prof_end(ev, st);
     }
-    if (sort)
+    if (merge)
+      BOS_CUDA(launch_merge_sort(merge_first, d_out, ws + pl.off_tmp, n, pl.R, (uint64_t*)(ws + pl.off_rstatus), st,
+                                 hooks));
+    else if (sort)
       for (uint32_t d = 0; d < pl.digits; ++d) {
         const int ev = prof_begin(st, kKRadix, 2.0 * n * pl.R, d);
         BOS_CUDA(launch_radix_pass(ra, pl.R, d, st));

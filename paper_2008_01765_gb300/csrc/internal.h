@@ -67,6 +67,20 @@ int orp_fast_occupancy(int R, int mode, uint32_t Z, uint32_t k, uint32_t C);
 cudaError_t launch_orp_fast(const PassArgs& a, int mode, uint32_t C, uint32_t max_clusters, cudaStream_t st,
                             int R, bool trace);
 
+// Stable merge sort by key (mergesort.cu): runs of 2048 sorted in shared memory, then merge
+// passes that double the run width. The result lands in buf0; the block-sorted runs are written
+// to buf0 when merge_passes(n) is even and to buf1 when it is odd, so `in` may be that buffer.
+// split: merge_split_entries(n) u64 of scratch. hooks (optional) bracket the block sort (stage 0)
+// and each merge pass (stage 1) with the algorithmic bytes.
+struct MergeHooks {
+  int (*begin)(cudaStream_t st, int stage, double bytes);
+  void (*end)(int slot, cudaStream_t st);
+};
+uint32_t merge_passes(uint64_t n);
+uint64_t merge_split_entries(uint64_t n);
+cudaError_t launch_merge_sort(const void* in, void* buf0, void* buf1, uint64_t n, int R, uint64_t* split,
+                              cudaStream_t st, const MergeHooks& hooks);
+
 // LSD radix sort (radix.cu)
 struct RadixArgs {
   const void* in;                 // histogram source (any order of the same multiset)

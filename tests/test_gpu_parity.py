@@ -268,6 +268,25 @@ def test_cluster_kernel_matches_generic_and_oracle(bos, n, Z, rec_bytes, k):
     assert outs["no_cluster"].max_cluster == 1
 
 
+MERGE_CASES = [
+    (1, 512, 16, "uniform"), (2047, 512, 8, "uniform"), (2048, 512, 16, "dup1024"), (2049, 512, 16, "uniform"),
+    (3 * 4096 + 5, 256, 16, "equal"), (1 << 16, 512, 8, "uniform"), (300001, 96, 16, "dup1024"),
+    (1 << 20, 1024, 16, "reverse"), (1 << 22, 1024, 16, "uniform"), ((1 << 21) + 777, 512, 8, "sorted"),
+]
+
+
+@pytest.mark.parametrize("n,Z,rec_bytes,dist", MERGE_CASES)
+def test_merge_sort_matches_oracle(bos, n, Z, rec_bytes, dist):
+    # The comparison-based sort after the ORP (stable merge sort) gives the oracle's stable sort of
+    # the ORP output: sizes around the 2048-record runs and merge chunks, odd and even numbers of
+    # merge passes, duplicate and equal keys (ties keep the ORP order), Z of the generic kernel.
+    recs = inputs.make_records(n, rec_bytes, dist, seed=n % 1000 + 3)
+    ref, rinfo = oracle.sort(recs, Z, 21, method=oracle.CLOSED, max_attempts=16)
+    got, info = gpu_sort(bos, recs, Z, 21, flags=bos.FLAG_MERGE_SORT, max_attempts=16)
+    assert info.attempts == rinfo.attempts and info.radix_passes == 0
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_cfg3_geometry_plans(bos):
     # n = 2^30 and Z = 1024 give L = 21. The fewest-passes plan uses 16-CTA clusters (7 levels a
     # pass); the measured-cost plan uses fewer levels per pass. Both give the oracle's result.
