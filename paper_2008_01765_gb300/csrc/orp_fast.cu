@@ -73,17 +73,6 @@ __device__ __forceinline__ void st_cluster_rec(uint32_t addr, const uint4& v) {
                : "memory");
 }
 
-// Lanes of the warp holding a real with the same k-bit digit (k ballots); 0 for dummies.
-__device__ __forceinline__ uint32_t peer_mask(uint32_t u, bool real, uint32_t k) {
-  uint32_t m = __ballot_sync(0xFFFFFFFFu, real);
-  for (uint32_t b = 0; b < k; ++b) {
-    const bool bit = (u >> b) & 1u;
-    const uint32_t bb = __ballot_sync(0xFFFFFFFFu, bit);
-    m &= bit ? bb : ~bb;
-  }
-  return real ? m : 0u;
-}
-
 struct FastLayout {
   uint32_t tile_rec, tile_tag, tags, rc, h, aggs, tot, moff, misc, total;
   uint32_t perm, perm_bytes;  // LAST: in-bin permutation scratch
@@ -334,7 +323,7 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
       uint32_t base = 0, total = 0;
       for (uint32_t c = 0; c < C; ++c) {
         const uint32_t x = aggs[c * D + u];
-        base += c < crank ? x : 0u;
+        if constexpr (CL) base += c < crank ? x : 0u;  // no earlier CTA without a cluster
         total += x;
       }
       tot[u] = total;

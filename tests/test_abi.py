@@ -82,3 +82,34 @@ def test_plan_geometry_matches_paper(bos):
     import oracle
     for n, Z in [(1 << 16, 512), (1 << 24, 512), (1 << 30, 1024)]:
         assert oracle.geometry(n, Z)[0] * Z >= 2 * n
+
+
+def test_plans_cover_every_level(bos):
+    # The planner (no device work with FLAG_PLAN_ONLY): for record widths, bucket sizes, sizes and
+    # cluster caps, a plan exists, its passes apply L levels (passes x max_k >= L), B matches
+    # Algorithm 3.1's smallest power of two with B*Z >= 2n, the cluster sizes respect the cap, and
+    # the fewest-passes plan never has more passes than the default, which never has more than the
+    # cluster-free one.
+    import oracle
+    for R in (8, 16):
+        for Z in (32, 64, 96, 256, 512, 1024, 2048, 4096):
+            for n in (1, 2, 100, 4097, 1 << 16, 300001, 1 << 22, (1 << 26) + 3, 1 << 30):
+                B, L = oracle.geometry(n, Z)
+                if B * Z >= 1 << 32:
+                    continue
+                plans = {}
+                for name, flags in (("auto", 0), ("fewest", bos.FLAG_FEWEST_PASSES),
+                                    ("nocl", bos.FLAG_NO_CLUSTER), ("cap2", bos.FLAG_MAX_CLUSTER(2)),
+                                    ("generic", bos.FLAG_GENERIC)):
+                    try:
+                        info = bos.plan(n, R, Z, flags=flags)
+                    except bos.BosError as e:  # beyond the documented Z range for 16-byte records
+                        assert name == "generic" and Z * R > 48 << 10 and e.status == bos.ERR_INVALID
+                        continue
+                    assert (info.B, info.L) == (B, L), (R, Z, n, name)
+                    assert info.passes >= 1 and info.passes * max(info.max_k, 1) >= L, (R, Z, n, name)
+                    plans[name] = info
+                assert plans["nocl"].max_cluster == 1
+                assert "generic" not in plans or plans["generic"].max_cluster == 1
+                assert plans["cap2"].max_cluster <= 2
+                assert plans["fewest"].passes <= plans["auto"].passes <= plans["nocl"].passes, (R, Z, n)
