@@ -199,8 +199,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"oblivious sort, n=2^{args.n_log2} 16-B records, Z={args.Z}",
-                       "sample_n": n},
+            "config": {"workload": f"sort n=2^{args.n_log2} rec16 Z={args.Z}", "n": 1 << args.n_log2,
+                       "rec_bytes": REC, "Z": args.Z, "keys": f"{args.dist} u64, payload = index",
+                       "sample_n": n, "parallelism": "one host thread"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
