@@ -19,6 +19,7 @@ FLAG_NO_CLUSTER = 0x4
 FLAG_FEWEST_PASSES = 0x8
 FLAG_PLAN_ONLY = 0x10
 FLAG_MERGE_SORT = 0x20
+FLAG_OBLIVIOUS_SPLIT = 0x40
 
 
 def FLAG_FORCE_OVERFLOW(n):

@@ -20,10 +20,10 @@ Trace g_trace{nullptr, 0};
 
 // ---- opt-in kernel timing (bos_profile_enable / bos_profile_read) ----
 enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKPerm,
-              kKMergeBlock, kKMerge, kKCount };
+              kKMergeBlock, kKMerge, kKOblivious, kKCount };
 const char* const kKNames[kKCount] = {"orp_pass_first", "orp_pass_mid", "orp_pass_last", "orp_pass_single",
                                      "radix_hist", "radix_prep", "radix_pass", "radix_pass_skipped",
-                                     "bitonic", "perm_table", "merge_block", "merge_pass"};
+                                     "bitonic", "perm_table", "merge_block", "merge_pass", "orp_oblivious"};
 constexpr int kMaxEv = 1024;
 struct Prof {
   bool on = false;
@@ -285,7 +285,7 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
   size_t off = 0;
   pl->off_ctrl = off; off = align256(off + sizeof(Ctrl));
   // two slot arrays whenever L >= 2 (the plain form needs both), so the size does not depend on k
-  const uint32_t arrays = L >= 2 ? 2 : L;
+  const uint32_t arrays = (L >= 2 || (p->flags & BOS_FLAG_OBLIVIOUS_SPLIT)) ? 2 : L;
   for (uint32_t x = 0; x < arrays; ++x) {
     pl->off_rec[x] = off; off = align256(off + slots * pl->R);
     pl->off_tag[x] = off; off = align256(off + slots * 4);
@@ -393,6 +393,43 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   const uint32_t max_attempts = p->max_attempts ? p->max_attempts : kDefaultAttempts;
   const uint32_t forced = (p->flags >> 8) & 0xFFu;
   const bool trace = g_trace.buf != nullptr;
+
+  if (p->flags & BOS_FLAG_OBLIVIOUS_SPLIT) {  // Section 4.1: bitonic MergeSplits, one launch per level
+    if (sort || oblivious_smem_bytes(pl.R, pl.Z) > kMaxSmem) return BOS_ERR_INVALID;
+    ObliviousArgs oa{};
+    oa.in = d_in;
+    oa.out = d_out;
+    for (int x = 0; x < 2; ++x) {
+      oa.rec[x] = ws + pl.off_rec[x];
+      oa.tag[x] = (uint32_t*)(ws + pl.off_tag[x]);
+    }
+    oa.load = (uint32_t*)(ws + pl.off_status);  // B words each: loads, then offsets
+    oa.off = oa.load + pl.B;
+    oa.part = (uint32_t*)(ws + pl.off_ord);
+    oa.n = n;
+    oa.B = pl.B;
+    oa.Z = pl.Z;
+    oa.L = pl.L;
+    oa.seed = p->seed;
+    oa.ctrl = ctrl;
+    oa.trace = g_trace;
+    const double slot_bytes = (double)pl.B * pl.Z * (pl.R + 4);
+    for (uint32_t attempt = 0; attempt < max_attempts; ++attempt) {
+      BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+      oa.attempt = attempt;
+      const int ev = prof_begin(st, kKOblivious, 2.0 * n * pl.R + slot_bytes * (2.0 * pl.L + 3.0));
+      BOS_CUDA(launch_oblivious_orp(oa, pl.R, st, trace));
+      prof_end(ev, st);
+      Ctrl h{};
+      BOS_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      BOS_CUDA(cudaStreamSynchronize(st));
+      if (g_prof.on) prof_collect(0);
+      if (info) info->attempts = attempt + 1;
+      if (h.overflow || attempt < forced) continue;
+      return BOS_OK;
+    }
+    return BOS_ERR_OVERFLOW;
+  }
   // the comparison sort (stable merge) in place of the radix sort; its block-sorted runs start
   // in the buffer that leaves the last merge pass's output in d_out
   const bool merge = sort && (p->flags & BOS_FLAG_MERGE_SORT);

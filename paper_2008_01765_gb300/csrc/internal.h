@@ -67,6 +67,25 @@ int orp_fast_occupancy(int R, int mode, uint32_t Z, uint32_t k, uint32_t C);
 cudaError_t launch_orp_fast(const PassArgs& a, int mode, uint32_t C, uint32_t max_clusters, cudaStream_t st,
                             int R, bool trace);
 
+// The ORP with O(1) client storage (oblivious.cu, Section 4.1): bitonic-sort MergeSplits, one
+// launch per level, bitonic in-bin permutations, a scan of the loads and the strip.
+struct ObliviousArgs {
+  const void* in;        // n input records
+  void* out;             // n output records
+  void* rec[2];          // slot record arrays (B*Z each), used in turn
+  uint32_t* tag[2];      // slot tag arrays
+  uint32_t* load;        // [B] reals per final bucket
+  uint32_t* off;         // [B] output offsets inside scan blocks
+  uint32_t* part;        // [B / 4096 + 1] scan block offsets
+  uint64_t n, B;
+  uint32_t Z, L, attempt;
+  uint64_t seed;
+  Ctrl* ctrl;
+  Trace trace;
+};
+uint32_t oblivious_smem_bytes(int R, uint32_t Z);
+cudaError_t launch_oblivious_orp(const ObliviousArgs& a, int R, cudaStream_t st, bool trace);
+
 // Stable merge sort by key (mergesort.cu): runs of 2048 sorted in shared memory, then merge
 // passes that double the run width. The result lands in buf0; the block-sorted runs are written
 // to buf0 when merge_passes(n) is even and to buf1 when it is odd, so `in` may be that buffer.

@@ -175,12 +175,12 @@ def test_batched_equals_alone(bos):
         np.testing.assert_array_equal(got[a:b], ref)
 
 
-def _trace(bos, recs, Z, seed, k=0):
+def _trace(bos, recs, Z, seed, k=0, flags=0):
     import torch
     buf = torch.zeros(1 << 27, dtype=torch.uint8, device="cuda")
     bos.trace_attach(buf)
     try:
-        gpu_orp(bos, recs, Z, seed, k=k)
+        gpu_orp(bos, recs, Z, seed, k=k, flags=flags)
         torch.cuda.synchronize()
     finally:
         bos.trace_attach(None)
@@ -211,6 +211,45 @@ def test_address_trace_is_input_independent(bos, k):
     np.testing.assert_array_equal(keep(t2), keep(base))
     # every slot of every bucket is read and written by each butterfly pass: counts check
     assert len(keep(base)) > 0
+
+
+OBLIVIOUS_CASES = [
+    (1, 2, 8), (3, 4, 16), (1000, 64, 8), (5000, 96, 16), (1 << 16, 512, 8), (300001, 256, 16),
+    ((1 << 18) + 5, 1024, 16), (20000, 4096, 8), (700, 8, 8),
+]
+
+
+@pytest.mark.parametrize("n,Z,rec_bytes", OBLIVIOUS_CASES)
+def test_oblivious_split_matches_oracle(bos, n, Z, rec_bytes):
+    # Section 4.1's form (bitonic MergeSplits, bitonic in-bin permutations) gives the oracle's ORP:
+    # L = 0, 1 and many levels, Z not a power of two, Z = 4096, and a small Z that overflows and
+    # retries (same attempts as the oracle, or overflow on every attempt on both sides).
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=n % 997 + 5)
+    seed = 0xABC + n
+    try:
+        ref, rinfo = oracle.orp(recs, Z, seed, max_attempts=16, method=oracle.CLOSED)
+    except oracle.OracleError as e:
+        assert e.status == oracle.ERR_OVERFLOW
+        with pytest.raises(bos.BosError) as ge:
+            gpu_orp(bos, recs, Z, seed, flags=bos.FLAG_OBLIVIOUS_SPLIT, max_attempts=16)
+        assert ge.value.status == bos.ERR_OVERFLOW
+        return
+    got, info = gpu_orp(bos, recs, Z, seed, flags=bos.FLAG_OBLIVIOUS_SPLIT, max_attempts=16)
+    assert info.attempts == rinfo.attempts
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_oblivious_split_trace_is_input_independent(bos):
+    # Every global access of the Section 4.1 form (placement, each level's bucket pairs, the final
+    # buckets, the strip) is the same multiset for different inputs of one size and seed.
+    n, Z = 1 << 12, 64
+    base = None
+    for dist in ("uniform", "equal", "sorted", "reverse"):
+        t = _trace(bos, inputs.make_records(n, 16, dist, seed=12), Z, seed=4, flags=bos.FLAG_OBLIVIOUS_SPLIT)
+        if base is None:
+            base = t
+        else:
+            np.testing.assert_array_equal(t, base)
 
 
 def test_cfg1_plain_form_full_size(bos):
