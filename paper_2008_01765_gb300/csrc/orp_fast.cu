@@ -256,24 +256,58 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
     load_rows(q, 0, rows0, rr);
     // FIRST: labels into the tag stage; later passes: wait for the tags' TMA
     if constexpr (FIRST) {
-      uint32_t sp = sp0, rrow = rr0;
-      uint64_t base;
-      uint32_t lim;
-      bucket_base(q, sp, base, lim);
-      for (uint32_t row = r0; row < r1; ++row) {
-        const uint32_t sl = rrow * 32 + lane;
-        uint32_t tg = kDummy;
-        if (rrow * 32 < lim) {  // rows past the group's records hold only dummies
-          if (sl < lim) tg = label_of(base + sl, a.seed, a.attempt, L);
-        }
-        tags[row * 32 + lane] = tg;
-        if (++rrow == rows_per_bucket) {
-          rrow = 0;
-          ++sp;
-          if (row + 1 < r1) bucket_base(q, sp, base, lim);
+      // Rows past a group's records hold only dummies (each warp writes its own); the rows with
+      // records are spread over all warps, two per step, so the labels' Philox chains overlap.
+      {
+        uint32_t sp = sp0, rrow = rr0;
+        uint64_t base;
+        uint32_t lim;
+        bucket_base(q, sp, base, lim);
+        for (uint32_t row = r0; row < r1; ++row) {
+          if (rrow * 32 >= lim) tags[row * 32 + lane] = kDummy;
+          if (++rrow == rows_per_bucket) {
+            rrow = 0;
+            ++sp;
+            if (row + 1 < r1) bucket_base(q, sp, base, lim);
+          }
         }
       }
-      __syncwarp();
+      // Data row d of the CTA lies in the first own bucket whose data rows, summed from bucket 0,
+      // exceed d. A thread's d only grows, so one cursor (bucket spc, its first data row dst)
+      // walks the buckets once.
+      uint32_t spc = 0, dst = 0, limc;
+      uint64_t basec;
+      bucket_base(q, 0, basec, limc);
+      auto data_row = [&](uint32_t d, uint32_t& row, uint64_t& base, uint32_t& lim) -> bool {
+        while (d >= dst + ((limc + 31) >> 5)) {
+          dst += (limc + 31) >> 5;
+          if (++spc >= Dc) return false;
+          bucket_base(q, spc, basec, limc);
+        }
+        row = spc * rows_per_bucket + (d - dst);
+        base = basec;
+        lim = limc;
+        return true;
+      };
+      for (uint32_t d0 = warp;; d0 += 2 * kW) {
+        uint32_t row0 = 0, row1 = 0, lim0 = 0, lim1 = 0;
+        uint64_t base0 = 0, base1 = 0;
+        if (!data_row(d0, row0, base0, lim0)) break;
+        const bool v1 = data_row(d0 + kW, row1, base1, lim1);
+        const uint32_t sl0 = (row0 - (row0 / rows_per_bucket) * rows_per_bucket) * 32 + lane;
+        if (v1) {
+          const uint32_t sl1 = (row1 - (row1 / rows_per_bucket) * rows_per_bucket) * 32 + lane;
+          const uint32_t t0 = label_of(base0 + sl0, a.seed, a.attempt, L);
+          const uint32_t t1 = label_of(base1 + sl1, a.seed, a.attempt, L);
+          tags[row0 * 32 + lane] = sl0 < lim0 ? t0 : kDummy;
+          tags[row1 * 32 + lane] = sl1 < lim1 ? t1 : kDummy;
+        } else {
+          const uint32_t t0 = label_of(base0 + sl0, a.seed, a.attempt, L);
+          tags[row0 * 32 + lane] = sl0 < lim0 ? t0 : kDummy;
+          break;
+        }
+      }
+      __syncthreads();  // rows were labelled by other warps
     } else {
       mbar_wait(bar, parity, a.ctrl);
       parity ^= 1u;
