@@ -13,17 +13,18 @@
 //     start of a subproblem so their latency overlaps the counting and the cluster exchange;
 //     the finished tile leaves by TMA bulk stores while the next subproblem starts.
 //   * Ranking is stable and warp-local: each warp owns a contiguous run of rows (32 slots) of
-//     the CTA's input stream, derives the peers of each slot with k ballots, and keeps running
-//     per-digit counters; a per-(warp, digit) prefix over warps and CTAs gives every real its
-//     output slot.
+//     the CTA's input stream, finds the peers of each slot with the match instruction (a warp
+//     holds at most 2^k + 1 distinct digits), and keeps running per-digit counters; a
+//     per-(warp, digit) prefix over warps and CTAs gives every real its output slot.
 // Every global address depends only on (n, Z, k, C, pass, subproblem): whole input buckets are
 // read, whole output buckets are written (Section 3.1). Label-dependent movement stays in shared
 // memory (local or distributed).
 //
-// LAST pass: the in-bin permutation of each final bucket (Section 3.2) depends only on the
-// bucket's load, known after the exchange, so it is built before the routing, in the still-empty
-// tile; after the routing each CTA writes its reals compacted, in permuted order, at the prefix of
-// the final loads found by a decoupled look-back over the subproblems (ticket order).
+// LAST pass: each final bucket's in-bin permutation (Section 3.2) arrives as a row of the table
+// that perm_table.cu sorted ahead of the pass (slots in key order, TMA-loaded per subproblem);
+// after the routing each CTA writes its reals compacted, in row order without the entries >= the
+// bucket's load, at the prefix of the final loads found by a decoupled look-back over the
+// subproblems (ticket order).
 #include "common.cuh"
 #include "internal.h"
 
