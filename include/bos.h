@@ -69,10 +69,10 @@ typedef enum {
 /* bos_sort: sort the ORP's output with a stable GPU merge sort (comparison-based, as Section 3.3
  * composes the ORP with a comparison sort) instead of the LSD radix sort. Same result. */
 #define BOS_FLAG_MERGE_SORT 0x20u
-/* bos_orp: the O(1)-client-storage form of Section 4.1. Every MergeSplit is one bitonic sort of its
- * two buckets (one launch per level), and every final bucket is permuted by one bitonic sort, so
- * the access schedule depends on neither the data nor the labels. Same result; much slower.
- * bos_sort rejects it (BOS_ERR_INVALID). */
+/* bos_orp, bos_sort: the ORP in the O(1)-client-storage form of Section 4.1. Every MergeSplit is one
+ * bitonic sort of its two buckets (one launch per level), and every final bucket is permuted by one
+ * bitonic sort, so the access schedule depends on neither the data nor the labels. Same result;
+ * much slower. */
 #define BOS_FLAG_OBLIVIOUS_SPLIT 0x40u
 /* Largest thread-block cluster a pass may use (1, 2, 4, 8 or 16; 0 = the library's choice).
  * Tuning only: the result never depends on it. */

@@ -394,11 +394,23 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   const uint32_t forced = (p->flags >> 8) & 0xFFu;
   const bool trace = g_trace.buf != nullptr;
 
-  if (p->flags & BOS_FLAG_OBLIVIOUS_SPLIT) {  // Section 4.1: bitonic MergeSplits, one launch per level
-    if (sort || oblivious_smem_bytes(pl.R, pl.Z) > kMaxSmem) return BOS_ERR_INVALID;
-    ObliviousArgs oa{};
+  // the comparison sort (stable merge) in place of the radix sort; its block-sorted runs start
+  // in the buffer that leaves the last merge pass's output in d_out
+  const bool merge = sort && (p->flags & BOS_FLAG_MERGE_SORT);
+  void* merge_first = merge ? ((merge_passes(n) & 1) ? (void*)(ws + pl.off_tmp) : d_out) : nullptr;
+  MergeHooks hooks{};
+  hooks.begin = [](cudaStream_t s2, int stage, double b) { return prof_begin(s2, stage ? kKMerge : kKMergeBlock, b); };
+  hooks.end = [](int slot, cudaStream_t s2) { prof_end(slot, s2); };
+  // Section 4.1's form of the ORP (bitonic MergeSplits, one launch per level) in place of the
+  // fused passes; its strip picks the output buffer the way the fused LAST pass does
+  const bool oblivious = (p->flags & BOS_FLAG_OBLIVIOUS_SPLIT) != 0;
+  if (oblivious && oblivious_smem_bytes(pl.R, pl.Z) > kMaxSmem) return BOS_ERR_INVALID;
+  ObliviousArgs oa{};
+  if (oblivious) {
     oa.in = d_in;
-    oa.out = d_out;
+    oa.out0 = merge ? merge_first : d_out;
+    oa.out1 = merge ? merge_first : (sort ? (void*)(ws + pl.off_tmp) : d_out);
+    oa.out_sel = (sort && !merge) ? 1u : 0u;
     for (int x = 0; x < 2; ++x) {
       oa.rec[x] = ws + pl.off_rec[x];
       oa.tag[x] = (uint32_t*)(ws + pl.off_tag[x]);
@@ -413,30 +425,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     oa.seed = p->seed;
     oa.ctrl = ctrl;
     oa.trace = g_trace;
-    const double slot_bytes = (double)pl.B * pl.Z * (pl.R + 4);
-    for (uint32_t attempt = 0; attempt < max_attempts; ++attempt) {
-      BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-      oa.attempt = attempt;
-      const int ev = prof_begin(st, kKOblivious, 2.0 * n * pl.R + slot_bytes * (2.0 * pl.L + 3.0));
-      BOS_CUDA(launch_oblivious_orp(oa, pl.R, st, trace));
-      prof_end(ev, st);
-      Ctrl h{};
-      BOS_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-      BOS_CUDA(cudaStreamSynchronize(st));
-      if (g_prof.on) prof_collect(0);
-      if (info) info->attempts = attempt + 1;
-      if (h.overflow || attempt < forced) continue;
-      return BOS_OK;
-    }
-    return BOS_ERR_OVERFLOW;
   }
-  // the comparison sort (stable merge) in place of the radix sort; its block-sorted runs start
-  // in the buffer that leaves the last merge pass's output in d_out
-  const bool merge = sort && (p->flags & BOS_FLAG_MERGE_SORT);
-  void* merge_first = merge ? ((merge_passes(n) & 1) ? (void*)(ws + pl.off_tmp) : d_out) : nullptr;
-  MergeHooks hooks{};
-  hooks.begin = [](cudaStream_t s2, int stage, double b) { return prof_begin(s2, stage ? kKMerge : kKMergeBlock, b); };
-  hooks.end = [](int slot, cudaStream_t s2) { prof_end(slot, s2); };
 
   RadixArgs ra{};
   if (sort && !merge) {
@@ -464,7 +453,14 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       BOS_CUDA(launch_radix_prep(ra, pl.R, st));
       prof_end(ev, st);
     }
-    for (uint32_t x = 0; x < pl.npass; ++x) {
+    if (oblivious) {
+      oa.attempt = attempt;
+      const double slot_bytes = (double)pl.B * pl.Z * (pl.R + 4);
+      const int ev = prof_begin(st, kKOblivious, 2.0 * n * pl.R + slot_bytes * (2.0 * pl.L + 3.0));
+      BOS_CUDA(launch_oblivious_orp(oa, pl.R, st, trace));
+      prof_end(ev, st);
+    }
+    for (uint32_t x = 0; x < (oblivious ? 0u : pl.npass); ++x) {
       PassArgs a{};
       const bool first = x == 0, last = x + 1 == pl.npass;
       const uint32_t src = (x + 1) & 1, dst = x & 1;  // pass x reads array (x-1)&1, writes x&1

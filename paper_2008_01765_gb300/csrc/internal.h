@@ -71,7 +71,9 @@ cudaError_t launch_orp_fast(const PassArgs& a, int mode, uint32_t C, uint32_t ma
 // launch per level, bitonic in-bin permutations, a scan of the loads and the strip.
 struct ObliviousArgs {
   const void* in;        // n input records
-  void* out;             // n output records
+  void* out0;            // n output records
+  void* out1;            // alternate output (sort scratch); used when out_sel and an odd number of
+  uint32_t out_sel;      // radix passes will run (as the fused LAST pass chooses)
   void* rec[2];          // slot record arrays (B*Z each), used in turn
   uint32_t* tag[2];      // slot tag arrays
   uint32_t* load;        // [B] reals per final bucket

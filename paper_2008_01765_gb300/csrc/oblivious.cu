@@ -315,7 +315,9 @@ template <int R, bool TRACE>
 __global__ void obl_strip_kernel(ObliviousArgs a, uint32_t src) {
   using Rec = typename RecT<R>::T;
   const Rec* brec = reinterpret_cast<const Rec*>(a.rec[src]);
-  Rec* out = reinterpret_cast<Rec*>(a.out);
+  Rec* out = reinterpret_cast<Rec*>(a.out0);
+  if (a.out_sel && (__popc(a.ctrl->radix_live) & 1)) out = reinterpret_cast<Rec*>(a.out1);
+  const uint32_t out_buf = (out == reinterpret_cast<Rec*>(a.out0)) ? kBufOut : kBufTmp;
   const uint32_t bufr = src ? kBufRecB : kBufRecA;
   for (uint64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
     const uint64_t o = (uint64_t)a.off[b] + a.part[b / kScanBlock];
@@ -324,7 +326,7 @@ __global__ void obl_strip_kernel(ObliviousArgs a, uint32_t src) {
       if (o + x < a.n) {
         out[o + x] = brec[b * a.Z + x];
         trace_log<TRACE>(a.trace, kRead, bufr, R, (b * a.Z + x) * R);
-        trace_log<TRACE>(a.trace, kWrite, kBufOut, R, (o + x) * R);
+        trace_log<TRACE>(a.trace, kWrite, out_buf, R, (o + x) * R);
       }
     }
   }

@@ -239,6 +239,21 @@ def test_oblivious_split_matches_oracle(bos, n, Z, rec_bytes):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("n,Z,rec_bytes,dist", [(1, 2, 16, "uniform"), (5000, 96, 16, "dup1024"),
+                                                 (1 << 16, 512, 8, "uniform"), (700, 8, 8, "sorted"),
+                                                 ((1 << 18) + 5, 1024, 16, "reverse")])
+def test_oblivious_split_sort_matches_oracle(bos, n, Z, rec_bytes, dist):
+    # The whole oblivious sort with Section 4.1's ORP, followed by the radix sort or by the merge
+    # sort, equals the oracle's stable sort of its ORP (ties in ORP order).
+    recs = inputs.make_records(n, rec_bytes, dist, seed=n % 991 + 7)
+    seed = 0xDEF + n
+    ref, rinfo = oracle.sort(recs, Z, seed, max_attempts=16, method=oracle.CLOSED)
+    for flags in (bos.FLAG_OBLIVIOUS_SPLIT, bos.FLAG_OBLIVIOUS_SPLIT | bos.FLAG_MERGE_SORT):
+        got, info = gpu_sort(bos, recs, Z, seed, flags=flags, max_attempts=16)
+        assert info.attempts == rinfo.attempts, flags
+        np.testing.assert_array_equal(got, ref, err_msg=str(flags))
+
+
 def test_oblivious_split_trace_is_input_independent(bos):
     # Every global access of the Section 4.1 form (placement, each level's bucket pairs, the final
     # buckets, the strip) is the same multiset for different inputs of one size and seed.
