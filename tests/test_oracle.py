@@ -165,6 +165,36 @@ def test_final_bucket_is_label_class_in_input_order():
         np.testing.assert_array_equal(np.sort(seg), np.flatnonzero(lab == b))
 
 
+def test_in_bin_order_is_the_sorted_slot_list_without_empty_slots():
+    # Section 3.2 orders a final bucket's m reals (slots 0..m-1) by (r(b, s), s), r the key from
+    # Philox(b*Z + s, attempt, stream 1). Dropping entries from a sorted list keeps the order of
+    # the rest, so the same order is the list of ALL Z slots sorted by (r, s) with the entries
+    # >= m removed (what the GPU's permutation table relies on). Both are checked against the
+    # oracle's output, bucket by bucket.
+    n, Z, seed = 5000, 64, 9
+    recs = inputs.make_records(n, 8, "uniform", seed=2)
+    out, info, loads = oracle.orp(recs, Z, seed, want_loads=True)
+    attempt = info.attempts - 1
+    lab = oracle.labels(n, seed, attempt, info.L)
+    offs = np.concatenate([[0], np.cumsum(loads)]).astype(np.int64)
+    for b in range(info.B):
+        idx = np.uint64(b * Z) + np.arange(Z, dtype=np.uint64)
+        ctr = np.zeros((Z, 4), dtype=np.uint32)
+        ctr[:, 0] = (idx & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
+        ctr[:, 2] = attempt
+        ctr[:, 3] = 1
+        key = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32), (Z, 1))
+        w = oracle.philox_many(ctr, key)
+        r = (w[:, 0].astype(np.uint64) << np.uint64(32)) | w[:, 1].astype(np.uint64)
+        m = int(loads[b])
+        reals_only = sorted(range(m), key=lambda s: (int(r[s]), s))
+        filtered = [s for s in sorted(range(Z), key=lambda s: (int(r[s]), s)) if s < m]
+        assert filtered == reals_only
+        members = np.flatnonzero(lab == b)  # slot s holds the s-th element of the class
+        np.testing.assert_array_equal(out["payload"][offs[b]:offs[b + 1]], members[reals_only])
+
+
 # --------------------------------------------------------------------------------------------
 # Lemma 3.3: the ORP output is a uniformly random permutation. n = 4 with Z = 4 (B = 2, no
 # overflow possible) and Z = 2 (B = 4; only the last level can overflow and that event is a
