@@ -74,6 +74,9 @@ typedef enum {
  * bitonic sort, so the access schedule depends on neither the data nor the labels. Same result;
  * much slower. */
 #define BOS_FLAG_OBLIVIOUS_SPLIT 0x40u
+/* Do not use the streaming pass kernel for the first and middle passes of the automatic plan
+ * (comparison and tests; the result is the same). */
+#define BOS_FLAG_NO_STREAM 0x80u
 /* Largest thread-block cluster a pass may use (1, 2, 4, 8 or 16; 0 = the library's choice).
  * Tuning only: the result never depends on it. */
 #define BOS_FLAG_MAX_CLUSTER(c) (((uint32_t)(c) & 0x1Fu) << 16)
@@ -98,6 +101,7 @@ typedef struct {
   uint64_t B;        /* number of buckets: smallest power of two with B * Z >= 2n */
   uint32_t max_cluster; /* largest thread-block cluster used by a pass (1 = no clusters) */
   uint32_t max_k;    /* most butterfly levels fused into one pass */
+  uint32_t stream_passes; /* passes run by the streaming kernel (first and middle passes) */
 } bos_info;
 
 /* Bytes of device workspace bos_orp / bos_sort need for n records under *p (0 for n = 0).

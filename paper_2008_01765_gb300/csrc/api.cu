@@ -78,6 +78,7 @@ struct Plan {
   uint32_t pass_k[kMaxPasses] = {};
   uint32_t pass_i[kMaxPasses] = {};
   uint32_t pass_C[kMaxPasses] = {};
+  bool pass_stream[kMaxPasses] = {};  // first / middle pass run by the streaming kernel (orp_stream.cu)
   // workspace offsets
   size_t off_ctrl = 0, off_rec[2] = {0, 0}, off_tag[2] = {0, 0}, off_status = 0;
   size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, off_ord = 0, total = 0;
@@ -204,6 +205,7 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
     static const double kMid[5] = {1.0, 1.371, 1.623, 1.919, 2.49};  // C = 1, 2, 4, 8, 16
     static const double kFirst[5] = {1.269, 1.496, 1.667, 2.168, 2.63};
     static const double kLast[5] = {1.219, 1.459, 1.723, 2.212, 2.63};
+    static const double kStreamFirst = 0.85, kStreamMid = 1.15;  // streaming kernel, k up to 8-9
     const uint32_t kcap = p->k ? p->k : kMaxKFast;
     auto c_for = [&](uint32_t k, bool last) -> uint32_t {  // smallest C holding k levels; 0: none
       if (k > kcap) return 0;
@@ -273,6 +275,53 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
       }
       pl->pass_k[bnp - 1] = bl;
       pl->pass_C[bnp - 1] = c_for(bl, true);
+      // The streaming kernel (orp_stream.cu) takes the first and middle passes when that is
+      // cheaper: up to 8-9 levels a pass with no cluster, the last pass stays the cluster kernel
+      // (it needs its final buckets whole for the in-bin permutation). Costs in the same unit.
+      const uint32_t kmin = orp_stream_min_k();
+      uint32_t ksf = (p->flags & BOS_FLAG_NO_STREAM) ? 0u : orp_stream_max_k(pl->R, p->Z, true, kMaxSmem);
+      uint32_t ksm = ksf ? orp_stream_max_k(pl->R, p->Z, false, kMaxSmem) : 0u;
+      if (p->k) {  // a caller-given k caps every pass (k = 1 is the plain form)
+        ksf = p->k >= kmin && ksf ? (ksf < p->k ? ksf : p->k) : 0u;
+        ksm = p->k >= kmin && ksm ? (ksm < p->k ? ksm : p->k) : 0u;
+      }
+      double sbest = 1e30;
+      uint32_t sl = 0, snp = 0;
+      for (uint32_t l = 1; ksf && l < L; ++l) {
+        const uint32_t Cl = c_for(l, true), S = L - l;
+        if (!Cl) continue;
+        for (uint32_t np = 1; np + 1 <= kMaxPasses; ++np) {
+          if (S < np * kmin || (np > 1 && !ksm)) continue;
+          if (S > ksf + (np - 1) * ksm) continue;
+          const double c = kStreamFirst + (np - 1) * kStreamMid + kLast[ci(Cl)];
+          if (c < sbest - 1e-9) {
+            sbest = c;
+            sl = l;
+            snp = np;
+          }
+          break;  // more stream passes only cost more
+        }
+      }
+      if (sl && sbest < bc - 1e-9) {
+        const uint32_t S = L - sl;
+        pl->npass = snp + 1;
+        // balanced split of S levels over snp passes, the first at most ksf, the others ksm
+        for (uint32_t x = 0; x < snp; ++x) {
+          pl->pass_k[x] = S / snp + (x < S % snp ? 1u : 0u);
+          pl->pass_C[x] = 1;
+          pl->pass_stream[x] = true;
+        }
+        while (pl->pass_k[0] > ksf) {  // move levels from the first pass to the middle ones
+          for (uint32_t x = 1; x < snp && pl->pass_k[0] > ksf; ++x)
+            if (pl->pass_k[x] < ksm) {
+              pl->pass_k[x]++;
+              pl->pass_k[0]--;
+            }
+        }
+        pl->pass_k[snp] = sl;
+        pl->pass_C[snp] = c_for(sl, true);
+        pl->pass_stream[snp] = false;
+      }
     }
   }
   uint32_t lvl = 0;
@@ -337,6 +386,7 @@ bos_status device_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl) {
     bool ok = true;
     for (uint32_t x = 0; x < pl->npass && ok; ++x) {
       const int mode = (x == 0 ? kModeFirst : 0) | (x + 1 == pl->npass ? kModeLast : 0);
+      if (pl->pass_stream[x]) continue;  // streaming passes: one CTA per SM, sized by the planner
       ok = fast_occupancy_cached(pl->R, mode, pl->Z, pl->pass_k[x], pl->pass_C[x]) > 0;
     }
     if (ok) return BOS_OK;
@@ -375,7 +425,9 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     info->B = pl.B;
     info->max_cluster = 1;
     info->max_k = 0;
+    info->stream_passes = 0;
     for (uint32_t x = 0; x < pl.npass; ++x) {
+      info->stream_passes += pl.pass_stream[x] ? 1u : 0u;
       info->max_cluster = pl.pass_C[x] > info->max_cluster ? pl.pass_C[x] : info->max_cluster;
       info->max_k = pl.pass_k[x] > info->max_k ? pl.pass_k[x] : info->max_k;
     }
@@ -524,7 +576,9 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         prof_end(evt, st);
       }
       const int ev = prof_begin(st, cls, in_b + out_b);
-      if (pl.fast)
+      if (pl.pass_stream[x])
+        BOS_CUDA(launch_orp_stream(a, first, st, pl.R, trace));
+      else if (pl.fast)
         BOS_CUDA(launch_orp_fast(a, mode, pl.pass_C[x], 0, st, pl.R, trace));
       else
         BOS_CUDA(launch_orp_pass(a, mode, pl.B >> a.k, st, pl.R, trace));

@@ -67,6 +67,14 @@ int orp_fast_occupancy(int R, int mode, uint32_t Z, uint32_t k, uint32_t C);
 cudaError_t launch_orp_fast(const PassArgs& a, int mode, uint32_t C, uint32_t max_clusters, cudaStream_t st,
                             int R, bool trace);
 
+// Streaming first / middle ORP pass (orp_stream.cu): one CTA per subproblem, input buckets
+// through a TMA ring, output chunks write-combined in shared memory; Z a multiple of 32, <= 2048.
+uint32_t orp_stream_smem_bytes(int R, uint32_t Z, uint32_t k, bool first);
+// Most levels a streaming pass holds in smem_limit bytes (0: the kernel cannot take this Z).
+uint32_t orp_stream_max_k(int R, uint32_t Z, bool first, uint32_t smem_limit);
+inline uint32_t orp_stream_min_k() { return 5; }
+cudaError_t launch_orp_stream(const PassArgs& a, bool first, cudaStream_t st, int R, bool trace);
+
 // The ORP with O(1) client storage (oblivious.cu, Section 4.1): bitonic-sort MergeSplits, one
 // launch per level, bitonic in-bin permutations, a scan of the loads and the strip.
 struct ObliviousArgs {

@@ -1,0 +1,402 @@
+// Streaming bucket ORP pass (sm_103a): the first pass and the middle passes of a fused plan.
+//
+// A pass applies k butterfly levels of Algorithm 3.1 (levels i..i+k-1): subproblem
+// q = G*2^i + t reads the input buckets G*2^(i+k) + s*2^i + t (s < 2^k) and writes the contiguous
+// output buckets q*2^k + u, each real going to u = label bits [L-1-i .. L-i-k], stable by (s, slot),
+// then dummies (the MergeSplit order of the butterfly; Figure 1).
+//
+// The persistent-cluster kernel (orp_fast.cu) holds all 2^k output buckets on chip, which caps k
+// by shared memory. This kernel streams instead: one CTA takes a whole subproblem and reads its
+// input buckets in order, each one (a "batch"; in the first pass, two groups of input records)
+// brought in by TMA bulk copies through a three-stage ring. Every output bucket owns a small ring
+// of kRing slots in shared memory; a real is appended to its bucket's ring at its stable rank, and
+// whenever a ring holds a whole chunk of kChunk slots the chunk leaves for HBM (coalesced 16-byte
+// stores). At the end of the subproblem every bucket's last partial chunk is padded with dummies
+// and its remaining chunks are written as dummies. So shared memory bounds the chunk buffers, not
+// the subproblem, and one pass applies up to 9 levels with no cluster.
+//
+// Obliviousness (Section 3.1): reads are whole input buckets (or the whole input range of the
+// groups); writes are whole chunks of kChunk slots, and every chunk of every output bucket is
+// written exactly once. The multiset of addresses is therefore a function of (n, Z, k, pass) alone;
+// only the order in which chunks leave depends on the labels, as in every GPU schedule here.
+//
+// Ranking inside a batch: each real takes a tentative ring position from a shared-memory atomic on
+// its bucket's counter and records its slot index there; after a barrier a real whose bucket got
+// several reals in this batch counts how many of them have a smaller slot index (usually zero to
+// three), which is its stable rank. If a batch would add more reals to a ring than it has room
+// for (rare: a ring keeps at most kChunk-1 slots between batches), the batch is redone in rounds
+// of kSub slots.
+//
+// Overflow (MergeSplit receives more than Z reals, Lemma 3.2): the level-(i+l) buckets of the
+// subproblem (l = 1..k-1) gather 2^l consecutive input buckets (2^(l-1) batches of the first pass)
+// and the digits with a common l-bit prefix; per-batch digit counts are folded into one counter
+// per (level, prefix) and checked at the end of each block. The final level is the ring's fill.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bos {
+
+namespace {
+
+constexpr int kST = 512;
+constexpr int kSW = kST / 32;
+constexpr uint32_t kChunk = 8;         // slots per HBM write (128 B of 16-byte records)
+constexpr uint32_t kRing = 24;         // ring slots per output bucket
+constexpr uint32_t kRingStride = 25;   // ring pitch in shared memory (odd: spreads the banks)
+constexpr uint32_t kStages = 3;        // input batches in flight
+constexpr uint32_t kMaxItems = 4;      // slots per thread per batch: Z <= 2048
+constexpr uint32_t kSub = 16;          // slots per round when a batch is redone (7 + 16 <= kRing)
+constexpr uint32_t kMinK = 5, kMaxK = 9;
+
+struct StreamLayout {
+  uint32_t ring_rec, ring_tag, aux, stage, stage_bytes, fill, done, cnt, lv, list, list_cap, misc, total;
+};
+
+__host__ __device__ inline uint32_t st_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_t k, bool first) {
+  const uint32_t D = 1u << k;
+  StreamLayout l{};
+  uint32_t off = 0;
+  l.ring_rec = off;
+  off = st_align(off + D * kRingStride * R, 16);
+  l.ring_tag = off;
+  off = st_align(off + D * kRingStride * 4, 16);
+  l.aux = off;
+  off = st_align(off + D * kRingStride * 2, 16);
+  // first pass: up to Z input records (two groups of at most Z/2) plus one record of alignment
+  l.stage_bytes = first ? st_align((Z + 2) * R, 128) : st_align(Z * (4 + R), 128);
+  l.stage = st_align(off, 128);
+  off = l.stage + kStages * l.stage_bytes;
+  l.fill = off;
+  off += D * 4;
+  l.done = off;
+  off += D * 4;
+  l.cnt = off;
+  off += 2 * D * 4;
+  l.lv = off;
+  off += D * 4;
+  l.list_cap = Z / kChunk + D;  // chunks one round can complete
+  l.list = off;
+  off += 2 * l.list_cap * 4;
+  l.misc = st_align(off, 16);
+  off = l.misc + 64;
+  l.total = off;
+  return l;
+}
+
+template <int R, bool FIRST, bool TRACE>
+__global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
+  using Rec = typename RecT<R>::T;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t Z = a.Z, k = a.k, D = 1u << k, L = a.L, i = a.i;
+  const uint32_t shift = L - i - k;
+  const StreamLayout lay = stream_layout(R, Z, k, FIRST);
+  Rec* ring_rec = reinterpret_cast<Rec*>(smem + lay.ring_rec);
+  uint32_t* ring_tag = reinterpret_cast<uint32_t*>(smem + lay.ring_tag);
+  uint16_t* aux = reinterpret_cast<uint16_t*>(smem + lay.aux);
+  uint32_t* fill = reinterpret_cast<uint32_t*>(smem + lay.fill);  // reals appended per bucket
+  uint32_t* done = reinterpret_cast<uint32_t*>(smem + lay.done);  // chunks written per bucket
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + lay.cnt);    // [2][D] reals per round
+  uint32_t* lv = reinterpret_cast<uint32_t*>(smem + lay.lv);      // level l, prefix p: lv[2^l - 2 + p]
+  uint32_t* list = reinterpret_cast<uint32_t*>(smem + lay.list);  // [2][list_cap] (bucket << 16 | chunk)
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + lay.misc);  // [kStages]
+  volatile uint32_t* flag = reinterpret_cast<volatile uint32_t*>(smem + lay.misc + 32);  // [2]
+  uint32_t* lcnt = reinterpret_cast<uint32_t*>(smem + lay.misc + 40);                    // [2]
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t nsub = a.B >> k;
+  const uint32_t NB = FIRST ? D / 2 : D;  // batches per subproblem
+  const uint64_t mysub = blockIdx.x < nsub ? (nsub - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const uint64_t nbatch = mysub * NB;
+  const Rec* in_first = reinterpret_cast<const Rec*>(a.in);
+  const Rec* in_rec = reinterpret_cast<const Rec*>(a.in_rec);
+  Rec* out_rec = reinterpret_cast<Rec*>(a.out_rec);
+  uint32_t* out_tag = a.out_tag;
+
+  for (uint32_t x = tid; x < D; x += kST) {
+    fill[x] = 0;
+    done[x] = 0;
+    cnt[x] = 0;
+    cnt[D + x] = 0;
+    lv[x] = 0;
+  }
+  if (tid == 0) {
+    for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(bars + s), 1);
+    flag[0] = flag[1] = 0;
+    lcnt[0] = lcnt[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  auto batch_q = [&](uint64_t g) -> uint64_t { return blockIdx.x + (g / NB) * gridDim.x; };
+  // first pass: batch s of subproblem q = groups q*D + 2s and q*D + 2s + 1 (B = 2^L)
+  auto first_range = [&](uint64_t q, uint32_t s, uint64_t& lo, uint64_t& hi) {
+    const uint64_t g0 = q * D + 2ull * s;
+    lo = (g0 * a.n) >> L;
+    hi = ((g0 + 2) * a.n) >> L;
+  };
+  // Input records [lo, hi) of a first-pass batch sit at stage index soff + (record - lo); the
+  // bulk copy takes [lo2, hi2), the largest sub-range whose global and shared addresses are both
+  // 16-byte aligned (d_in is only guaranteed rec_bytes alignment).
+  const uint32_t in_odd = R == 8 ? (uint32_t)((reinterpret_cast<uintptr_t>(a.in) >> 3) & 1u) : 0u;
+  auto first_bulk = [&](uint64_t lo, uint64_t hi, uint64_t& lo2, uint64_t& hi2, uint32_t& soff) {
+    if (R == 8) {
+      lo2 = lo + ((lo + in_odd) & 1u);  // (d_in + 8 * lo2) is a multiple of 16
+      hi2 = hi - ((hi + in_odd) & 1u);
+      soff = (uint32_t)((lo2 - lo) & 1u);  // so that lo2's stage index is even
+    } else {
+      lo2 = lo;
+      hi2 = hi;
+      soff = 0;
+    }
+  };
+  auto in_bucket = [&](uint64_t q, uint32_t s) -> uint64_t {
+    const uint64_t t = q & ((1ull << i) - 1), G = q >> i;
+    return (G << (i + k)) + ((uint64_t)s << i) + t;
+  };
+  // TMA of batch g into its stage (thread 0)
+  auto issue = [&](uint64_t g) {
+    const uint32_t st = (uint32_t)(g % kStages);
+    const uint32_t bar = smem_u32(bars + st);
+    const uint32_t dst = smem_u32(smem + lay.stage + st * lay.stage_bytes);
+    const uint64_t q = batch_q(g);
+    const uint32_t s = (uint32_t)(g % NB);
+    if constexpr (FIRST) {
+      uint64_t lo, hi;
+      first_range(q, s, lo, hi);
+      // a bulk copy starts and ends on 16-byte addresses: 8-byte records at the odd ends are
+      // loaded by a thread (first_bulk)
+      uint64_t lo2, hi2;
+      uint32_t soff;
+      first_bulk(lo, hi, lo2, hi2, soff);
+      const uint32_t bytes = hi2 > lo2 ? (uint32_t)((hi2 - lo2) * R) : 0u;
+      mbar_expect_tx(bar, bytes);
+      if (bytes) tma_load(dst + (uint32_t)((lo2 - lo + soff) * R), in_first + lo2, bytes, bar);
+      trace_log<TRACE>(a.trace, kRead, kBufIn, (uint32_t)((hi - lo) * R), lo * R);
+    } else {
+      const uint64_t bk = in_bucket(q, s);
+      mbar_expect_tx(bar, Z * (4 + R));
+      tma_load(dst, a.in_tag + bk * Z, Z * 4, bar);
+      tma_load(dst + Z * 4, in_rec + bk * Z, Z * R, bar);
+      trace_log<TRACE>(a.trace, kRead, a.buf_in_tag, Z * 4, bk * Z * 4);
+      trace_log<TRACE>(a.trace, kRead, a.buf_in_rec, Z * R, bk * Z * R);
+    }
+  };
+
+  if (tid == 0)
+    for (uint64_t g = 0; g < kStages && g < nbatch; ++g) issue(g);
+
+  for (uint64_t g = 0; g < nbatch; ++g) {
+    const uint64_t q = batch_q(g);
+    const uint32_t s = (uint32_t)(g % NB), st = (uint32_t)(g % kStages);
+    const uint32_t par = (uint32_t)((g / kStages) & 1), pb = (uint32_t)(g & 1);
+    unsigned char* stg = smem + lay.stage + st * lay.stage_bytes;
+    const uint32_t* stag = reinterpret_cast<const uint32_t*>(stg);
+    Rec* srec = reinterpret_cast<Rec*>(FIRST ? stg : stg + Z * 4);
+    uint64_t lo = 0, hi = 0;
+    uint32_t nslot = Z, soff = 0;
+    if constexpr (FIRST) {
+      first_range(q, s, lo, hi);
+      nslot = (uint32_t)(hi - lo);
+      uint64_t lo2, hi2;
+      first_bulk(lo, hi, lo2, hi2, soff);
+      if (R == 8 && tid == kST - 1) {  // the records the bulk copy leaves out (odd ends)
+        if (hi2 <= lo2) {  // at most two records, no bulk part
+          for (uint32_t x = 0; x < nslot; ++x) srec[soff + x] = in_first[lo + x];
+        } else {
+          if (lo2 > lo) srec[soff] = in_first[lo];
+          if (hi2 < hi) srec[soff + nslot - 1] = in_first[hi - 1];
+        }
+      }
+    } else {
+      mbar_wait(smem_u32(bars + st), par, a.ctrl);
+    }
+    const uint64_t obase = q * D;
+    uint32_t* cntp = cnt + pb * D;
+    uint32_t* listp = list + pb * lay.list_cap;
+
+    // One round over batch slots [rlo, rhi). check: give up (false) if a ring would overflow.
+    auto round = [&](uint32_t rlo, uint32_t rhi, bool check) -> bool {
+      if (tid == 0) lcnt[pb] = 0;
+      uint32_t iu[kMaxItems], ifl[kMaxItems], itg[kMaxItems];
+      // ---- A: tentative positions (atomics) and each real's slot index at its position ----
+#pragma unroll
+      for (uint32_t j = 0; j < kMaxItems; ++j) {
+        const uint32_t x = rlo + tid + j * kST;
+        iu[j] = D;
+        ifl[j] = 0;
+        itg[j] = kDummy;
+        if (x < rhi) {
+          uint32_t tg;
+          if constexpr (FIRST)
+            tg = label_of(lo + x, a.seed, a.attempt, L);
+          else
+            tg = stag[x];
+          itg[j] = tg;
+          if (tg != kDummy) {
+            const uint32_t u = (tg >> shift) & (D - 1);
+            const uint32_t f = fill[u];
+            const uint32_t t = atomicAdd(&cntp[u], 1u);
+            aux[u * kRingStride + (f + t) % kRing] = (uint16_t)x;
+            if (check && t + (f - kChunk * done[u]) >= kRing) flag[pb] = 1u;
+            iu[j] = u;
+            ifl[j] = f;
+          }
+        }
+      }
+      __syncthreads();
+      if (check && flag[pb]) {  // a ring would overflow: undo the counts
+#pragma unroll
+        for (uint32_t j = 0; j < kMaxItems; ++j)
+          if (iu[j] < D) cntp[iu[j]] = 0u;
+        __syncthreads();
+        return false;
+      }
+      if constexpr (FIRST) mbar_wait(smem_u32(bars + st), par, a.ctrl);
+      // ---- B: stable rank, append to the ring, completed chunks to the write list ----
+#pragma unroll
+      for (uint32_t j = 0; j < kMaxItems; ++j) {
+        if (iu[j] < D) {
+          const uint32_t u = iu[j], f = ifl[j], x = rlo + tid + j * kST, c = cntp[u];
+          uint32_t r = 0;
+          if (c > 1)
+            for (uint32_t cc = 0; cc < c; ++cc) r += aux[u * kRingStride + (f + cc) % kRing] < x ? 1u : 0u;
+          const uint32_t pos = u * kRingStride + (f + r) % kRing;
+          ring_rec[pos] = srec[soff + x];
+          ring_tag[pos] = itg[j];
+          if (r == 0) {
+            const uint32_t nf = f + c;
+            fill[u] = nf;
+            for (uint32_t ch = f / kChunk; ch < nf / kChunk; ++ch)
+              if (ch * kChunk < Z) listp[atomicAdd(&lcnt[pb], 1u)] = (u << 16) | ch;
+            done[u] = nf / kChunk;
+          }
+        }
+      }
+      // level counters: per-digit counts of this round summed over groups of 2^g digits
+      if ((uint32_t)tid < D) {
+        uint32_t v = cntp[tid];
+        for (uint32_t gsz = 1; gsz < k; ++gsz) {
+          const uint32_t l = k - gsz;
+          if (gsz <= 5) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, 1u << (gsz - 1));
+            if ((tid & ((1u << gsz) - 1)) == 0 && v) lv[(1u << l) - 2 + (tid >> gsz)] += v;
+          } else if (lane == 0 && v) {
+            atomicAdd(&lv[(1u << l) - 2 + (tid >> gsz)], v);
+          }
+        }
+      }
+      __syncthreads();
+      // ---- C: write the completed chunks (four per warp instruction) ----
+      const uint32_t nl = lcnt[pb];
+      for (uint32_t e0 = warp * 4; e0 < nl; e0 += kSW * 4) {
+        const uint32_t e = e0 + (lane >> 3), jj = lane & 7;
+        if (e < nl) {
+          const uint32_t w = listp[e], u = w >> 16, slot = (w & 0xFFFFu) * kChunk + jj;
+          const uint32_t pos = u * kRingStride + slot % kRing;
+          const uint64_t o = (obase + u) * Z + slot;
+          out_rec[o] = ring_rec[pos];
+          out_tag[o] = ring_tag[pos];
+          if (jj == 0) {
+            trace_log<TRACE>(a.trace, kWrite, a.buf_out_rec, kChunk * R, o * R);
+            trace_log<TRACE>(a.trace, kWrite, a.buf_out_tag, kChunk * 4, o * 4);
+          }
+        }
+      }
+      if ((uint32_t)tid < D) cntp[tid] = 0;
+      return true;
+    };
+
+    if (!round(0, nslot, true)) {
+      for (uint32_t sb = 0; sb < nslot; sb += kSub) {
+        round(sb, min(sb + kSub, nslot), false);
+        __syncthreads();  // the next round reuses this round's counters and list
+      }
+    }
+    // ---- after the batch: its stage is free; level blocks that end here are checked ----
+    if (tid == 0) {
+      flag[pb] = 0u;
+      if (g + kStages < nbatch) issue(g + kStages);
+    }
+    for (uint32_t t = tid; t + 2 < D; t += kST) {
+      const uint32_t l = 31 - __clz(t + 2);
+      const uint32_t span = FIRST ? (1u << (l - 1)) : (1u << l);  // batches per level-l block
+      if (((s + 1) & (span - 1)) == 0) {
+        if (lv[t] > Z) atomicExch(&a.ctrl->overflow, 1u);
+        lv[t] = 0;
+      }
+    }
+    if (s == NB - 1) {
+      // ---- end of the subproblem: the last partial chunk of every bucket padded with dummies,
+      // then its remaining chunks as dummies; the final loads are checked against Z ----
+      for (uint32_t u = warp; u < D; u += kSW) {
+        const uint32_t f = fill[u], d = done[u];
+        if (lane == 0 && f > Z) atomicExch(&a.ctrl->overflow, 1u);
+        const uint64_t ob = (obase + u) * Z;
+        for (uint32_t slot = d * kChunk + lane; slot < Z; slot += 32) {
+          const bool real = slot < f;
+          const uint32_t pos = u * kRingStride + slot % kRing;
+          out_rec[ob + slot] = real ? ring_rec[pos] : RecT<R>::zero();
+          out_tag[ob + slot] = real ? ring_tag[pos] : kDummy;
+          if ((slot & (kChunk - 1)) == 0) {
+            trace_log<TRACE>(a.trace, kWrite, a.buf_out_rec, kChunk * R, (ob + slot) * R);
+            trace_log<TRACE>(a.trace, kWrite, a.buf_out_tag, kChunk * 4, (ob + slot) * 4);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          fill[u] = 0;
+          done[u] = 0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int R, bool FIRST, bool TRACE>
+cudaError_t stream_launch(const PassArgs& a, cudaStream_t st) {
+  const uint32_t smem = stream_layout(R, a.Z, a.k, FIRST).total;
+  auto kern = orp_stream_kernel<R, FIRST, TRACE>;
+  cudaError_t e = set_smem_optin(kern);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kST, smem)) != cudaSuccess) return e;
+  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const uint64_t nsub = a.B >> a.k;
+  uint64_t grid = (uint64_t)per_sm * sms;
+  if (grid > nsub) grid = nsub;
+  if (grid == 0) return cudaSuccess;
+  kern<<<(unsigned)grid, kST, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t orp_stream_smem_bytes(int R, uint32_t Z, uint32_t k, bool first) {
+  return stream_layout(R, Z, k, first).total;
+}
+
+uint32_t orp_stream_max_k(int R, uint32_t Z, bool first, uint32_t smem_limit) {
+  if (Z % 32 != 0 || Z > kMaxItems * kST) return 0;
+  uint32_t best = 0;
+  for (uint32_t k = kMinK; k <= kMaxK; ++k)
+    if (stream_layout(R, Z, k, first).total <= smem_limit) best = k;
+  return best;
+}
+
+cudaError_t launch_orp_stream(const PassArgs& a, bool first, cudaStream_t st, int R, bool trace) {
+  if (a.k < kMinK || a.k > kMaxK || a.Z % 32 != 0 || a.Z > kMaxItems * kST || a.i + a.k > a.L)
+    return cudaErrorInvalidValue;
+  if (R == 8) {
+    if (first) return trace ? stream_launch<8, true, true>(a, st) : stream_launch<8, true, false>(a, st);
+    return trace ? stream_launch<8, false, true>(a, st) : stream_launch<8, false, false>(a, st);
+  }
+  if (first) return trace ? stream_launch<16, true, true>(a, st) : stream_launch<16, true, false>(a, st);
+  return trace ? stream_launch<16, false, true>(a, st) : stream_launch<16, false, false>(a, st);
+}
+
+}  // namespace bos

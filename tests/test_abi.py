@@ -91,8 +91,8 @@ def test_plans_cover_every_level(bos):
     # The planner (no device work with FLAG_PLAN_ONLY): for record widths, bucket sizes, sizes and
     # cluster caps, a plan exists, its passes apply L levels (passes x max_k >= L), B matches
     # Algorithm 3.1's smallest power of two with B*Z >= 2n, the cluster sizes respect the cap, and
-    # the fewest-passes plan never has more passes than the default, which never has more than the
-    # cluster-free one.
+    # the fewest-passes plan never has more passes than the default without the streaming kernel,
+    # which never has more than the cluster-free one.
     import oracle
     for R in (8, 16):
         for Z in (32, 64, 96, 256, 512, 1024, 2048, 4096):
@@ -101,8 +101,9 @@ def test_plans_cover_every_level(bos):
                 if B * Z >= 1 << 32:
                     continue
                 plans = {}
-                for name, flags in (("auto", 0), ("fewest", bos.FLAG_FEWEST_PASSES),
+                for name, flags in (("auto", 0), ("nostream", bos.FLAG_NO_STREAM), ("fewest", bos.FLAG_FEWEST_PASSES),
                                     ("nocl", bos.FLAG_NO_CLUSTER), ("cap2", bos.FLAG_MAX_CLUSTER(2)),
+                                    ("nocl_nostream", bos.FLAG_NO_CLUSTER | bos.FLAG_NO_STREAM),
                                     ("generic", bos.FLAG_GENERIC)):
                     try:
                         info = bos.plan(n, R, Z, flags=flags)
@@ -115,4 +116,9 @@ def test_plans_cover_every_level(bos):
                 assert plans["nocl"].max_cluster == 1
                 assert "generic" not in plans or plans["generic"].max_cluster == 1
                 assert plans["cap2"].max_cluster <= 2
-                assert plans["fewest"].passes <= plans["auto"].passes <= plans["nocl"].passes, (R, Z, n)
+                assert plans["fewest"].passes <= plans["nostream"].passes <= plans["nocl_nostream"].passes, (R, Z, n)
+                # the streaming kernel (no clusters) is chosen only where it needs no more passes
+                assert plans["auto"].passes <= plans["nostream"].passes, (R, Z, n)
+                assert plans["nocl"].passes <= plans["nocl_nostream"].passes, (R, Z, n)
+                assert plans["nostream"].stream_passes == 0
+                assert "generic" not in plans or plans["generic"].stream_passes == 0

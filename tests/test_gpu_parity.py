@@ -310,7 +310,9 @@ def test_cluster_kernel_matches_generic_and_oracle(bos, n, Z, rec_bytes, k):
             assert ge.value.status == bos.ERR_OVERFLOW
         return
     outs = {}
-    for name, flags in (("auto", 0), ("fewest", bos.FLAG_FEWEST_PASSES), ("no_cluster", bos.FLAG_NO_CLUSTER),
+    for name, flags in (("auto", 0), ("no_stream", bos.FLAG_NO_STREAM), ("fewest", bos.FLAG_FEWEST_PASSES),
+                        ("no_cluster", bos.FLAG_NO_CLUSTER),
+                        ("no_cluster_no_stream", bos.FLAG_NO_CLUSTER | bos.FLAG_NO_STREAM),
                         ("generic", bos.FLAG_GENERIC)):
         got, info = gpu_orp(bos, recs, Z, seed, k=k, flags=flags, max_attempts=16)
         assert info.attempts == rinfo.attempts, name
@@ -318,7 +320,8 @@ def test_cluster_kernel_matches_generic_and_oracle(bos, n, Z, rec_bytes, k):
         outs[name] = info
     if Z % 32 == 0 and k == 0 and outs["auto"].L >= 8:
         assert outs["fewest"].max_cluster > 1
-        assert outs["fewest"].passes <= outs["auto"].passes <= outs["no_cluster"].passes
+        assert outs["fewest"].passes <= outs["no_stream"].passes <= outs["no_cluster_no_stream"].passes
+        assert outs["auto"].passes <= outs["no_stream"].passes
     assert outs["no_cluster"].max_cluster == 1
 
 
@@ -412,3 +415,97 @@ def test_batched_retries_only_overflowing_arrays(bos):
         pytest.skip(f"an array exhausted its attempts: {e}")
     assert (att >= 1).all() and (att > 1).any()
     _check_batch_against_oracle(recs, offs, seeds, ops, Zs, bos.to_host(out, recs.dtype), att)
+
+
+STREAM_CASES = [
+    # (n, Z, rec_bytes, k): automatic plans whose first and middle passes run the streaming kernel
+    # (orp_stream.cu). Ragged n (groups of unequal size), the Z values it takes, both widths.
+    ((1 << 20) + 3, 512, 16, 0), (1 << 20, 256, 8, 0), (300001, 96, 8, 0), (4097, 64, 8, 0),
+    (1 << 21, 2048, 16, 0), ((1 << 22) + 12345, 1024, 16, 0), (1 << 24, 512, 16, 0), (1 << 21, 64, 8, 0),
+    # k = 5 with Z = 2048: a batch brings 32-64 reals to each of the 32 output buckets, more than a
+    # ring holds, so every batch is redone in rounds of 16 slots (the kernel's slow path)
+    (1 << 20, 2048, 8, 5), ((1 << 20) + 1, 2048, 16, 5), (1 << 20, 1024, 16, 6),
+]
+
+
+@pytest.mark.parametrize("n,Z,rec_bytes,k", STREAM_CASES)
+def test_stream_pass_matches_oracle(bos, n, Z, rec_bytes, k):
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=(n * 7 + Z) % 100003)
+    seed = 0x5EED + n
+    plan = bos.plan(n, rec_bytes, Z, k=k, sort=False)
+    assert plan.stream_passes >= 1
+    try:
+        ref, rinfo = oracle.orp(recs, Z, seed, max_attempts=16, method=oracle.CLOSED)
+    except oracle.OracleError as e:
+        assert e.status == oracle.ERR_OVERFLOW
+        with pytest.raises(bos.BosError) as ge:
+            gpu_orp(bos, recs, Z, seed, k=k, max_attempts=16)
+        assert ge.value.status == bos.ERR_OVERFLOW
+        return
+    got, info = gpu_orp(bos, recs, Z, seed, k=k, max_attempts=16)
+    assert info.attempts == rinfo.attempts and info.stream_passes == plan.stream_passes
+    np.testing.assert_array_equal(got, ref)
+    got2, info2 = gpu_orp(bos, recs, Z, seed, k=k, max_attempts=16, flags=bos.FLAG_NO_STREAM)
+    assert info2.stream_passes == 0
+    np.testing.assert_array_equal(got2, ref)
+
+
+def test_stream_pass_overflow_and_retry(bos):
+    # Z = 32 at n = 2^14 (B = 2^10) overflows in most attempts (Lemma 3.2); the streaming first
+    # pass must flag exactly the attempts the oracle flags, intermediate levels included.
+    recs = inputs.make_records(1 << 14, 16, "uniform", seed=8)
+    seen = 0
+    for seed in range(40):
+        try:
+            ref, rinfo = oracle.orp(recs, 32, seed, max_attempts=8, method=oracle.CLOSED)
+        except oracle.OracleError:
+            with pytest.raises(bos.BosError):
+                gpu_orp(bos, recs, 32, seed, max_attempts=8, k=5)
+            continue
+        got, info = gpu_orp(bos, recs, 32, seed, max_attempts=8, k=5)
+        assert info.stream_passes >= 1
+        assert info.attempts == rinfo.attempts
+        seen += info.attempts > 1
+        np.testing.assert_array_equal(got, ref)
+    assert seen > 0
+
+
+@pytest.mark.parametrize("n", [100003, 1 << 20])
+def test_stream_first_pass_8_byte_aligned_input(bos, n):
+    # d_in need only be aligned to the record size: the first pass's bulk copies must start on a
+    # 16-byte address, so 8-byte records at either end of a batch are loaded separately.
+    import torch
+    recs = inputs.make_records(n, 8, "uniform", seed=31)
+    buf = torch.empty(n * 8 + 16, dtype=torch.uint8, device="cuda")
+    x = buf[8:8 + n * 8]
+    x.copy_(bos.to_device(recs))
+    assert x.data_ptr() % 16 == 8
+    ref, rinfo = oracle.orp(recs, 256, 3, method=oracle.CLOSED)
+    out, info = bos.orp(x, 8, Z=256, seed=3)
+    assert info.stream_passes >= 1 and info.attempts == rinfo.attempts
+    np.testing.assert_array_equal(bos.to_host(out, recs.dtype), ref)
+    sref, _ = oracle.sort(recs, 256, 3, method=oracle.CLOSED)
+    sout, _ = bos.sort(x, 8, Z=256, seed=3)
+    np.testing.assert_array_equal(bos.to_host(sout, recs.dtype), sref)
+
+
+def test_stream_trace_is_input_and_seed_independent(bos):
+    # The streaming pass reads whole input ranges and buckets and writes every 8-slot chunk of every
+    # output bucket once: its address multiset depends on neither the input nor the seed.
+    n, Z = 1 << 18, 256
+    assert bos.plan(n, 16, Z, sort=False).stream_passes >= 1
+    base = None
+    for dist in ("uniform", "equal", "sorted", "reverse"):
+        t = _trace(bos, inputs.make_records(n, 16, dist, seed=12), Z, seed=4)
+        if base is None:
+            base = t
+        else:
+            np.testing.assert_array_equal(t, base)
+    t2 = _trace(bos, inputs.make_records(n, 16, "uniform", seed=12), Z, seed=99)
+    kind_buf = lambda t: ((t[:, 0] >> np.uint64(48)) & np.uint64(0xFF))
+    keep = lambda t: t[kind_buf(t) != 5]
+    np.testing.assert_array_equal(keep(t2), keep(base))
+    # the first pass wrote every chunk of the B*Z slot array exactly once
+    B = 1 << 11
+    wr_tag = base[(kind_buf(base) == 2) & ((base[:, 0] >> np.uint64(56)) == 2)]
+    assert len(wr_tag) >= B * Z // 8
