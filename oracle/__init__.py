@@ -37,6 +37,7 @@ def lib():
         L.or_philox_many.argtypes = [_u64, _vp, _vp, _vp]
         L.or_geometry.argtypes = [_u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]
         L.or_labels.argtypes = [_u64, _u64, _u32, _u32, _vp]
+        L.or_group_bounds.argtypes = [_u64, _u32, _vp]
         L.or_overflow.argtypes = [_u64, _u32, _u64, _u32, ctypes.c_int]
         L.or_overflow.restype = ctypes.c_int
         L.or_overflow_count.argtypes = [_u64, _u32, _u64, _u64, _u32, ctypes.c_int]
@@ -102,6 +103,14 @@ def geometry(n, Z):
     B, L = _u64(), _u32()
     lib().or_geometry(n, Z, ctypes.byref(B), ctypes.byref(L))
     return B.value, L.value
+
+
+def group_bounds(n, Z):
+    """Boundaries of the B groups of Algorithm 3.1's placement: group j = [b[j], b[j+1])."""
+    B, _ = geometry(n, Z)
+    out = np.zeros(B + 1, dtype=np.uint64)
+    lib().or_group_bounds(n, Z, _ptr(out))
+    return out
 
 
 def labels(n, seed, attempt, L):

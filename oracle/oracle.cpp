@@ -302,6 +302,15 @@ void or_philox_many(uint64_t count, const uint32_t* ctrs, const uint32_t* keys, 
 
 void or_geometry(uint64_t n, uint32_t Z, uint64_t* B, uint32_t* L) { geometry(n, Z, B, L); }
 
+// Test hook: the boundaries out[j] = group_lo(j), j = 0..B, of the B groups Algorithm 3.1's
+// placement divides the input into (the literal and closed forms both place by these).
+void or_group_bounds(uint64_t n, uint32_t Z, uint64_t* out) {
+  uint64_t B;
+  uint32_t L;
+  geometry(n, Z, &B, &L);
+  for (uint64_t j = 0; j <= B; ++j) out[j] = group_lo(j, n, B);
+}
+
 void or_labels(uint64_t n, uint64_t seed, uint32_t attempt, uint32_t L, uint32_t* out) {
   for (uint64_t i = 0; i < n; ++i) out[i] = label_of(i, seed, attempt, L);
 }

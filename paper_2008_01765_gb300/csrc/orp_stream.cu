@@ -35,21 +35,20 @@
 #include "internal.h"
 
 namespace bos {
-
 namespace {
 
-constexpr int kST = 512;
+constexpr int kST = 1024;
 constexpr int kSW = kST / 32;
 constexpr uint32_t kChunk = 8;         // slots per HBM write (128 B of 16-byte records)
 constexpr uint32_t kRing = 24;         // ring slots per output bucket
 constexpr uint32_t kRingStride = 25;   // ring pitch in shared memory (odd: spreads the banks)
 constexpr uint32_t kStages = 3;        // input batches in flight
-constexpr uint32_t kMaxItems = 4;      // slots per thread per batch: Z <= 2048
+constexpr uint32_t kMaxItems = 2;      // slots per thread per batch: Z <= 2048
 constexpr uint32_t kSub = 16;          // slots per round when a batch is redone (7 + 16 <= kRing)
 constexpr uint32_t kMinK = 5, kMaxK = 9;
 
 struct StreamLayout {
-  uint32_t ring_rec, ring_tag, aux, stage, stage_bytes, fill, done, cnt, lv, list, list_cap, misc, total;
+  uint32_t ring_rec, ring_tag, aux, stage, stage_bytes, fill, done, cnt, lv, misc, total;
 };
 
 __host__ __device__ inline uint32_t st_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -76,9 +75,6 @@ __host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_
   off += 2 * D * 4;
   l.lv = off;
   off += D * 4;
-  l.list_cap = Z / kChunk + D;  // chunks one round can complete
-  l.list = off;
-  off += 2 * l.list_cap * 4;
   l.misc = st_align(off, 16);
   off = l.misc + 64;
   l.total = off;
@@ -99,10 +95,8 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
   uint32_t* done = reinterpret_cast<uint32_t*>(smem + lay.done);  // chunks written per bucket
   uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + lay.cnt);    // [2][D] reals per round
   uint32_t* lv = reinterpret_cast<uint32_t*>(smem + lay.lv);      // level l, prefix p: lv[2^l - 2 + p]
-  uint32_t* list = reinterpret_cast<uint32_t*>(smem + lay.list);  // [2][list_cap] (bucket << 16 | chunk)
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + lay.misc);  // [kStages]
   volatile uint32_t* flag = reinterpret_cast<volatile uint32_t*>(smem + lay.misc + 32);  // [2]
-  uint32_t* lcnt = reinterpret_cast<uint32_t*>(smem + lay.misc + 40);                    // [2]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t nsub = a.B >> k;
@@ -124,12 +118,10 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
   if (tid == 0) {
     for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(bars + s), 1);
     flag[0] = flag[1] = 0;
-    lcnt[0] = lcnt[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  auto batch_q = [&](uint64_t g) -> uint64_t { return blockIdx.x + (g / NB) * gridDim.x; };
   // first pass: batch s of subproblem q = groups q*D + 2s and q*D + 2s + 1 (B = 2^L)
   auto first_range = [&](uint64_t q, uint32_t s, uint64_t& lo, uint64_t& hi) {
     const uint64_t g0 = q * D + 2ull * s;
@@ -155,13 +147,10 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     const uint64_t t = q & ((1ull << i) - 1), G = q >> i;
     return (G << (i + k)) + ((uint64_t)s << i) + t;
   };
-  // TMA of batch g into its stage (thread 0)
-  auto issue = [&](uint64_t g) {
-    const uint32_t st = (uint32_t)(g % kStages);
+  // TMA of batch s of subproblem q into stage st (thread 0)
+  auto issue = [&](uint64_t q, uint32_t s, uint32_t st) {
     const uint32_t bar = smem_u32(bars + st);
     const uint32_t dst = smem_u32(smem + lay.stage + st * lay.stage_bytes);
-    const uint64_t q = batch_q(g);
-    const uint32_t s = (uint32_t)(g % NB);
     if constexpr (FIRST) {
       uint64_t lo, hi;
       first_range(q, s, lo, hi);
@@ -184,13 +173,67 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     }
   };
 
-  if (tid == 0)
-    for (uint64_t g = 0; g < kStages && g < nbatch; ++g) issue(g);
+  // Writes every whole chunk of the subproblem's output buckets not yet written (done[u] counts
+  // the chunks written; chunks at or past Z are never written: that bucket overflowed).
+  auto flush_chunks = [&](uint64_t obase) {
+    const uint32_t jj = lane & 7, grp = lane >> 3;
+    for (uint32_t ub = 0; ub < D; ub += 32 * kSW) {
+      const uint32_t u = ub + lane * kSW + warp;
+      uint32_t d = 0, nch = 0;
+      if (u < D) {
+        d = done[u];
+        const uint32_t c1 = min(fill[u] / kChunk, Z / kChunk);
+        nch = c1 > d ? c1 - d : 0u;
+      }
+      uint32_t mask = __ballot_sync(0xFFFFFFFFu, nch > 0);
+      while (mask) {
+        uint32_t mm = mask;  // this 8-lane group serves the grp-th set lane of the mask
+        for (uint32_t z = 0; z < grp && mm; ++z) mm &= mm - 1;
+        const int src = mm ? __ffs(mm) - 1 : 0;
+        const uint32_t su = __shfl_sync(0xFFFFFFFFu, u, src), sd = __shfl_sync(0xFFFFFFFFu, d, src);
+        if (mm) {
+          const uint32_t slot = sd * kChunk + jj, pos = su * kRingStride + slot % kRing;
+          const uint64_t o = (obase + su) * Z + slot;
+          out_rec[o] = ring_rec[pos];
+          out_tag[o] = ring_tag[pos];
+          if (jj == 0) {
+            trace_log<TRACE>(a.trace, kWrite, a.buf_out_rec, kChunk * R, o * R);
+            trace_log<TRACE>(a.trace, kWrite, a.buf_out_tag, kChunk * 4, o * 4);
+          }
+        }
+        uint32_t rest = mask;  // the (up to) four lowest set lanes were served
+        for (int z = 0; z < 4 && rest; ++z) rest &= rest - 1;
+        if ((mask ^ rest) >> lane & 1u) {
+          ++d;
+          --nch;
+        }
+        mask = __ballot_sync(0xFFFFFFFFu, nch > 0);
+      }
+      if (u < D) done[u] = d;
+    }
+  };
 
+  // Batch cursor (q, s) with its stage st and mbarrier parity par, advanced without division;
+  // thread 0 keeps a second cursor kStages batches ahead for the TMA issue.
+  uint64_t iq = blockIdx.x;
+  uint32_t is = 0, ist = 0;
+  uint64_t issued = 0;
+  auto issue_next = [&]() {
+    issue(iq, is, ist);
+    ++issued;
+    if (++is == NB) {
+      is = 0;
+      iq += gridDim.x;
+    }
+    if (++ist == kStages) ist = 0;
+  };
+  if (tid == 0)
+    while (issued < kStages && issued < nbatch) issue_next();
+
+  uint64_t q = blockIdx.x;
+  uint32_t s = 0, st = 0, par = 0;
   for (uint64_t g = 0; g < nbatch; ++g) {
-    const uint64_t q = batch_q(g);
-    const uint32_t s = (uint32_t)(g % NB), st = (uint32_t)(g % kStages);
-    const uint32_t par = (uint32_t)((g / kStages) & 1), pb = (uint32_t)(g & 1);
+    const uint32_t pb = (uint32_t)(g & 1);
     unsigned char* stg = smem + lay.stage + st * lay.stage_bytes;
     const uint32_t* stag = reinterpret_cast<const uint32_t*>(stg);
     Rec* srec = reinterpret_cast<Rec*>(FIRST ? stg : stg + Z * 4);
@@ -214,11 +257,9 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     }
     const uint64_t obase = q * D;
     uint32_t* cntp = cnt + pb * D;
-    uint32_t* listp = list + pb * lay.list_cap;
 
     // One round over batch slots [rlo, rhi). check: give up (false) if a ring would overflow.
     auto round = [&](uint32_t rlo, uint32_t rhi, bool check) -> bool {
-      if (tid == 0) lcnt[pb] = 0;
       uint32_t iu[kMaxItems], ifl[kMaxItems], itg[kMaxItems];
       // ---- A: tentative positions (atomics) and each real's slot index at its position ----
 #pragma unroll
@@ -254,7 +295,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
         return false;
       }
       if constexpr (FIRST) mbar_wait(smem_u32(bars + st), par, a.ctrl);
-      // ---- B: stable rank, append to the ring, completed chunks to the write list ----
+      // ---- B: stable rank, append to the ring ----
 #pragma unroll
       for (uint32_t j = 0; j < kMaxItems; ++j) {
         if (iu[j] < D) {
@@ -265,13 +306,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
           const uint32_t pos = u * kRingStride + (f + r) % kRing;
           ring_rec[pos] = srec[soff + x];
           ring_tag[pos] = itg[j];
-          if (r == 0) {
-            const uint32_t nf = f + c;
-            fill[u] = nf;
-            for (uint32_t ch = f / kChunk; ch < nf / kChunk; ++ch)
-              if (ch * kChunk < Z) listp[atomicAdd(&lcnt[pb], 1u)] = (u << 16) | ch;
-            done[u] = nf / kChunk;
-          }
+          if (r == 0) fill[u] = f + c;
         }
       }
       // level counters: per-digit counts of this round summed over groups of 2^g digits
@@ -288,22 +323,9 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
         }
       }
       __syncthreads();
-      // ---- C: write the completed chunks (four per warp instruction) ----
-      const uint32_t nl = lcnt[pb];
-      for (uint32_t e0 = warp * 4; e0 < nl; e0 += kSW * 4) {
-        const uint32_t e = e0 + (lane >> 3), jj = lane & 7;
-        if (e < nl) {
-          const uint32_t w = listp[e], u = w >> 16, slot = (w & 0xFFFFu) * kChunk + jj;
-          const uint32_t pos = u * kRingStride + slot % kRing;
-          const uint64_t o = (obase + u) * Z + slot;
-          out_rec[o] = ring_rec[pos];
-          out_tag[o] = ring_tag[pos];
-          if (jj == 0) {
-            trace_log<TRACE>(a.trace, kWrite, a.buf_out_rec, kChunk * R, o * R);
-            trace_log<TRACE>(a.trace, kWrite, a.buf_out_tag, kChunk * 4, o * 4);
-          }
-        }
-      }
+      // ---- C: write the completed chunks. Lane l of warp w watches bucket l * kSW + w; the
+      // buckets with a whole unwritten chunk are served four at a time (8 lanes per chunk) ----
+      flush_chunks(obase);
       if ((uint32_t)tid < D) cntp[tid] = 0;
       return true;
     };
@@ -311,23 +333,24 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     if (!round(0, nslot, true)) {
       for (uint32_t sb = 0; sb < nslot; sb += kSub) {
         round(sb, min(sb + kSub, nslot), false);
-        __syncthreads();  // the next round reuses this round's counters and list
+        __syncthreads();  // the next round reuses this round's counters
       }
     }
     // ---- after the batch: its stage is free; level blocks that end here are checked ----
     if (tid == 0) {
       flag[pb] = 0u;
-      if (g + kStages < nbatch) issue(g + kStages);
+      if (issued < nbatch) issue_next();
     }
-    for (uint32_t t = tid; t + 2 < D; t += kST) {
-      const uint32_t l = 31 - __clz(t + 2);
-      const uint32_t span = FIRST ? (1u << (l - 1)) : (1u << l);  // batches per level-l block
-      if (((s + 1) & (span - 1)) == 0) {
+    {  // level l's blocks end after every 2^l batches (2^(l-1) in the first pass): its 2^l counters
+      const uint32_t e = FIRST ? __ffs(~s) : __ffs(~s) - 1;  // levels 1..e end here
+      const uint32_t lmax = e < k - 1 ? e : k - 1;
+      for (uint32_t t = tid; t + 2 < (2u << lmax); t += kST) {
         if (lv[t] > Z) atomicExch(&a.ctrl->overflow, 1u);
         lv[t] = 0;
       }
     }
     if (s == NB - 1) {
+      __syncthreads();  // every chunk written by the flushes is counted in done[]
       // ---- end of the subproblem: the last partial chunk of every bucket padded with dummies,
       // then its remaining chunks as dummies; the final loads are checked against Z ----
       for (uint32_t u = warp; u < D; u += kSW) {
@@ -352,6 +375,14 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
       }
       __syncthreads();
     }
+    if (++s == NB) {
+      s = 0;
+      q += gridDim.x;
+    }
+    if (++st == kStages) {
+      st = 0;
+      par ^= 1u;
+    }
   }
 }
 
@@ -375,6 +406,7 @@ cudaError_t stream_launch(const PassArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
 
 uint32_t orp_stream_smem_bytes(int R, uint32_t Z, uint32_t k, bool first) {
   return stream_layout(R, Z, k, first).total;

@@ -143,6 +143,43 @@ def test_literal_equals_closed_form(n, Z):
             assert loads.sum() == n
 
 
+@pytest.mark.parametrize("n,Z", [(5, 2), (37, 3), (1000, 8), (4097, 64), (12345, 12), (300001, 96),
+                                 (99991, 512), (64, 4), (1 << 12, 32), (3, 4)])
+def test_groups_divide_the_input_evenly(n, Z):
+    # Algorithm 3.1 "evenly divides X into B groups": every group has floor(n/B) or ceil(n/B)
+    # elements, the groups tile [0, n) in order, exactly n mod B of them are the larger size, and
+    # none is larger than Z/2 rounded up (so a padded bucket always holds its group).
+    B, L = oracle.geometry(n, Z)
+    b = oracle.group_bounds(n, Z).astype(np.int64)
+    assert b.size == B + 1 and b[0] == 0 and b[-1] == n
+    sizes = np.diff(b)
+    assert (sizes >= 0).all()
+    assert set(np.unique(sizes)) <= {n // B, -(-n // B)}
+    assert int((sizes == -(-n // B)).sum()) == (n % B if n % B else B)
+    assert sizes.max() <= -(-Z // 2)
+
+
+def test_literal_overflow_follows_the_groups():
+    # The literal butterfly overflows exactly when some level-i bucket gathers more than Z reals,
+    # where level-i bucket (G, t) holds the elements of groups [G 2^i, (G+1) 2^i) whose top i label
+    # bits are t. Counted here by brute force from the exported group bounds and labels, for sizes
+    # B does not divide, so an uneven split would change the outcome on some seed.
+    for n, Z in [(5, 2), (37, 3), (97, 6), (200, 8), (1000, 12)]:
+        B, L = oracle.geometry(n, Z)
+        assert n % B != 0
+        grp = np.repeat(np.arange(B), np.diff(oracle.group_bounds(n, Z).astype(np.int64)))
+        seen = set()
+        for seed in range(200):
+            lab = oracle.labels(n, seed, 0, L).astype(np.int64)
+            over = False
+            for i in range(1, L + 1):
+                cell = ((grp >> i) << i) | (lab >> (L - i))
+                over |= np.bincount(cell, minlength=B).max() > Z
+            assert oracle.overflow(n, Z, seed, 0, oracle.LITERAL) == over, (n, Z, seed)
+            seen.add(over)
+        assert seen == {False, True}, (n, Z)
+
+
 def test_overflow_literal_equals_closed_form():
     # Small Z makes overflow frequent at every level; both forms must agree seed by seed.
     for n, Z in [(64, 4), (200, 8), (37, 3), (512, 16), (96, 6)]:
