@@ -81,7 +81,7 @@ struct Plan {
   bool pass_stream[kMaxPasses] = {};  // first / middle pass run by the streaming kernel (orp_stream.cu)
   // workspace offsets
   size_t off_ctrl = 0, off_rec[2] = {0, 0}, off_tag[2] = {0, 0}, off_status = 0;
-  size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, off_ord = 0, total = 0;
+  size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, off_ord = 0, off_load = 0, total = 0;
   uint64_t orp_tiles = 0, radix_tiles = 0;
 };
 
@@ -341,6 +341,7 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
   }
   pl->orp_tiles = B >> pl->pass_k[pl->npass - 1];
   pl->off_ord = off; off = align256(off + slots * 2);  // in-bin permutation table (u16 per slot)
+  pl->off_load = off; off = align256(off + B * 4);     // final loads, counted for the table
   // sized for the largest last pass (k = 1) so the workspace does not depend on k
   pl->off_status = off; off = align256(off + B * 8);
   if (sort) {
@@ -560,6 +561,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       if (last && pl.fast) {  // the LAST pass's in-bin permutation table for this attempt
         PermTableArgs ta{};
         ta.ord = (uint16_t*)(ws + pl.off_ord);
+        ta.load = (uint32_t*)(ws + pl.off_load);
         ta.tag = first ? nullptr : a.in_tag;  // a single pass has no input tags: rows of all Z slots
         ta.B = pl.B;
         ta.Z = pl.Z;

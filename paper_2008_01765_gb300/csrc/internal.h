@@ -35,10 +35,12 @@ struct PassArgs {
 // In-bin permutation table (perm_table.cu): row b < B lists final bucket b's slots in the order
 // of the Section 3.2 keys of (b, attempt, seed), ord[b*Z + rank] = slot. With the LAST pass's
 // input tags (tag != null; levels i..i+k-1 of L) a row holds the bucket's m real slots, then
-// 0xFFFF; without them, all Z slots. Z a multiple of 32, <= 4096; k <= 12.
+// 0xFFFF, m counted first into load[b] by a kernel of its own; without them, all Z slots. Z a
+// multiple of 32, <= 4096; k <= 12.
 struct PermTableArgs {
   uint16_t* ord;
   const uint32_t* tag;
+  uint32_t* load;        // [B] reals per final bucket (workspace), written and read here
   uint64_t B;
   uint32_t Z, attempt, i, k, L, buf_tag;
   uint64_t seed;
