@@ -17,9 +17,11 @@
  * rest of the record is payload and is never compared.
  *
  * Conventions for every entry point:
- *   - Every pointer named d_* is a device pointer owned by the caller. The library never
- *     allocates or frees device memory, never prints and never aborts; it reports errors by
- *     status (host-side scratch of the batched calls is ordinary heap memory).
+ *   - Every pointer named d_* is a device pointer owned by the caller. No call allocates or
+ *     frees device memory, prints or aborts; errors are reported by status (host-side scratch of
+ *     the batched calls is ordinary heap memory). The library image itself holds one fixed
+ *     device array, the BOS_NOALLOC_SCRATCH_BYTES scratch of bos_orp_noalloc, on every GPU
+ *     where its kernels are loaded.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is stream-ordered.
  *     bos_orp / bos_sort / bos_sort_batched synchronise `stream` once per attempt to read the
  *     overflow flag (Algorithm 3.1, MergeSplit aborts on overflow; the call retries with a
@@ -104,8 +106,10 @@ typedef struct {
   uint32_t stream_passes; /* passes run by the streaming kernel (first and middle passes) */
 } bos_info;
 
-/* Bytes of device workspace bos_orp / bos_sort need for n records under *p (0 for n = 0).
- * Returns 0 and sets nothing on invalid parameters. */
+/* Bytes of device workspace bos_orp / bos_sort need for n records under *p (0 for n = 0):
+ * the two bucket arrays of Algorithm 3.1 (B * Z slots each, the paper's log B + 1 arrays used in
+ * turn), the in-bin permutation table of Section 3.2 and, for bos_sort, the radix sort's scratch
+ * (Section 3.3). Returns 0 and sets nothing on invalid parameters. */
 size_t bos_workspace_bytes(uint64_t n, const bos_params* p);
 
 /* Bucket ORP (Algorithm 3.1 + Section 3.2): d_out[0..n) = d_in permuted uniformly at random
@@ -116,19 +120,22 @@ bos_status bos_orp(const void* d_in, void* d_out, uint64_t n, const bos_params* 
                    size_t ws_bytes, void* stream, bos_info* info);
 
 /* Bucket ORP for callers that cannot allocate device memory (the paper has no counterpart; this
- * is a deployment aid). Callers such as code running inside a device allocator's callbacks, code
- * running during a relaxed or global-mode stream capture, real-time loops that may not risk an
- * allocation's implicit synchronisation, or plugins whose host owns all device memory cannot
- * provide the workspace bos_orp needs. bos_orp_noalloc gives the same result as bos_orp for the
- * same arguments but takes its workspace from a scratch array compiled into the library:
+ * is a deployment aid). Some callers cannot provide the workspace bos_orp needs: code running
+ * inside a custom device allocator or its callbacks (allocating there would re-enter the
+ * allocator), and plugins whose host owns all device memory and forbids them to allocate.
+ * bos_orp_noalloc gives the same result as bos_orp for the same arguments but takes its workspace
+ * from a scratch array compiled into the library:
  *   - size: BOS_NOALLOC_SCRATCH_BYTES (64 MiB) of device memory, held on every GPU where the
  *     library's kernels are loaded until the process exits. n is accepted while the ORP's
  *     workspace for n fits; otherwise the call returns BOS_ERR_WORKSPACE and touches nothing.
  *     (bos_workspace_bytes(n, p) <= BOS_NOALLOC_SCRATCH_BYTES is a sufficient check; with
  *     Z = 512 every n <= 2^19 fits for 16-byte records and every n <= 2^20 for 8-byte records.)
- *   - no allocation: the call makes no cudaMalloc / cudaFree or other allocating call. Its first
- *     call on a device looks up the scratch's device address (cudaGetSymbolAddress, with that
- *     device current); make that first call before any stream capture on the device.
+ *   - no allocation: the call makes no cudaMalloc / cudaFree or other allocating call. Every call
+ *     looks up the scratch's device address on the current device (cudaGetSymbolAddress); on the
+ *     first call on a device that lookup also loads the library's kernels there.
+ *   - synchronisation: like bos_orp, the call synchronises `stream` after every attempt to read
+ *     the overflow flag (Algorithm 3.1's MergeSplit abort), so it blocks the host until the ORP
+ *     has finished and must not be issued on a stream that is being captured.
  *   - sharing: every call on a device uses the same scratch, which keeps the previous call's
  *     contents (the call clears what must start at zero itself). Calls whose GPU work overlaps
  *     (different streams, or host threads) race on the scratch and give wrong results: order
@@ -192,8 +199,20 @@ bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t 
  * kind: 1 = read, 2 = write. buffer: 0 = input, 1 = slot records A, 2 = slot tags A,
  * 3 = slot records B, 4 = slot tags B, 5 = output, 6 = sort scratch in the workspace,
  * 7 = in-bin permutation table in the workspace. Attach NULL to detach. The trace run uses
- * separate kernel instances; the results are identical. */
+ * separate kernel instances; the results are identical. The buffer is process-wide: every call
+ * that starts while it is attached, from any host thread, appends to it (each call reads the
+ * attachment once when it starts); attach and detach between calls to trace one call alone. */
 bos_status bos_trace_attach(void* d_buf, size_t bytes);
+
+/* Debug address-trace digest (obliviousness check at sizes whose full trace would not fit,
+ * Section 3.1 and Lemma 3.3). While attached, every access the trace above would record is folded
+ * into d_buf instead: d_buf holds 256 slots of two uint64 words, and slot (SM id mod 256) counts
+ * its entries in word 0 and adds SplitMix64's mix of the entry (mix(word0 ^ mix(offset))) to word 1
+ * modulo 2^64. The sums over all slots of both words depend only on the multiset of entries. The
+ * caller zeroes the buffer first; bytes >= 4096. Attach NULL (to either attach call) to detach.
+ * Same sharing rule as bos_trace_attach. The batched calls carry the buffer attached when their
+ * descriptors were written (bos_batched_prepare) and log while one is attached at enqueue. */
+bos_status bos_trace_attach_digest(void* d_buf, size_t bytes);
 
 /* Self-test hook for the random source (Philox4x32-10, Salmon et al. SC 2011) that draws the
  * labels of Algorithm 3.1 and the in-bin permutation keys of Section 3.2. For i < n it writes
@@ -208,7 +227,11 @@ bos_status bos_selftest_philox(const uint32_t* d_ctr, const uint32_t* d_key, uin
  * stream; each kernel class accumulates its launches, device milliseconds and algorithmic bytes
  * (whole slot arrays read and written by a butterfly pass; records read and written by a radix
  * pass; keys read by the histogram). bos_profile_enable creates its events on the first call
- * (CUDA events, no device memory) and resets the totals; not thread-safe. */
+ * (CUDA events, no device memory) and resets the totals. The totals are process-wide: calls from
+ * several host threads may run while profiling is on (the counters are guarded, and a pair of
+ * events whose launch has not finished when another thread collects stays pending); switching
+ * profiling on or off, or reading the totals, while other threads run calls mixes their launches
+ * into the figures. */
 typedef struct {
   char name[32];     /* orp_pass_first, orp_pass_mid, orp_pass_last, orp_pass_single, radix_hist,
                         radix_prep, radix_pass, radix_pass_skipped, bitonic */
@@ -221,6 +244,7 @@ bos_status bos_profile_enable(int on);
  * number of kernel launches counted since the last enable. Returns the entries written. */
 uint32_t bos_profile_read(bos_kernel_stat* out, uint32_t max, uint64_t* total_launches);
 
+/* Text of a status code (no counterpart in the paper). */
 const char* bos_status_str(bos_status s);
 
 /* Library version, (major << 16) | minor. */

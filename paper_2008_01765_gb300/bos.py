@@ -91,6 +91,8 @@ def lib():
         L.bos_bitonic_sort.restype = ctypes.c_int
         L.bos_trace_attach.argtypes = [_vp, ctypes.c_size_t]
         L.bos_trace_attach.restype = ctypes.c_int
+        L.bos_trace_attach_digest.argtypes = [_vp, ctypes.c_size_t]
+        L.bos_trace_attach_digest.restype = ctypes.c_int
         L.bos_status_str.argtypes = [ctypes.c_int]
         L.bos_status_str.restype = ctypes.c_char_p
         L.bos_version.restype = _u32
@@ -282,6 +284,15 @@ def trace_attach(buf):
     else:
         _check(lib().bos_trace_attach(_vp(buf.data_ptr()), buf.numel() * buf.element_size()),
                "bos_trace_attach")
+
+
+def trace_attach_digest(buf):
+    """Attach a zeroed CUDA tensor (>= 4096 bytes) as the address-trace digest (None detaches)."""
+    if buf is None:
+        _check(lib().bos_trace_attach_digest(None, 0), "bos_trace_attach_digest")
+    else:
+        _check(lib().bos_trace_attach_digest(_vp(buf.data_ptr()), buf.numel() * buf.element_size()),
+               "bos_trace_attach_digest")
 
 
 def selftest_philox(ctr, key, with_curand=True, stream=None):

@@ -1,7 +1,9 @@
 // C ABI of libbos (declared in include/bos.h): argument checks, pass planning, workspace layout
 // and the attempt loop of Algorithm 3.1 (retry with a fresh attempt counter on overflow).
+#include <atomic>
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "bos.h"
@@ -16,7 +18,17 @@ constexpr uint32_t kMaxPasses = 32;
 constexpr uint32_t kMaxLevels = 32;  // L < 32: slot indexes are 32-bit
 constexpr uint32_t kDefaultAttempts = 8;
 
-Trace g_trace{nullptr, 0};
+// Process-wide debug state. The trace buffer is read once per call under g_state_mu, so an
+// attach from one thread never tears a call's copy; the profiling events and totals are updated
+// under the same mutex and the launch counter is atomic, so calls from several host threads
+// (the serving loop's workers) are safe while profiling is on (their launches are then timed in
+// whatever order the threads record them).
+std::mutex g_state_mu;
+Trace g_trace{nullptr, 0, 0};
+Trace trace_snapshot() {
+  std::lock_guard<std::mutex> g(g_state_mu);
+  return g_trace;
+}
 
 // ---- opt-in kernel timing (bos_profile_enable / bos_profile_read) ----
 enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKPerm,
@@ -26,7 +38,7 @@ const char* const kKNames[kKCount] = {"orp_pass_first", "orp_pass_mid", "orp_pas
                                      "bitonic", "perm_table", "merge_block", "merge_pass", "orp_oblivious"};
 constexpr int kMaxEv = 1024;
 struct Prof {
-  bool on = false;
+  std::atomic<bool> on{false};
   bool created = false;
   cudaEvent_t ev[2 * kMaxEv];
   int pending = 0;
@@ -36,13 +48,15 @@ struct Prof {
   uint64_t launches[kKCount] = {};
   double ms[kKCount] = {};
   double alg_bytes[kKCount] = {};
-  uint64_t total_launches = 0;
+  std::atomic<uint64_t> total_launches{0};
 };
 Prof g_prof;
 
 // Records an event pair around one launch when profiling is on. Returns the slot or -1.
 int prof_begin(cudaStream_t st, int cls, double bytes, uint32_t digit = 0) {
-  g_prof.total_launches++;
+  g_prof.total_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof.on) return -1;
+  std::lock_guard<std::mutex> g(g_state_mu);
   if (!g_prof.on || g_prof.pending >= kMaxEv) return -1;
   const int i = g_prof.pending++;
   g_prof.cls[i] = cls;
@@ -56,16 +70,32 @@ void prof_end(int i, cudaStream_t st) {
 }
 // Folds the finished event pairs into the per-class totals (the stream has been synchronised).
 void prof_collect(uint32_t radix_live) {
+  std::lock_guard<std::mutex> g(g_state_mu);
+  int keep = 0;  // pairs whose end has not been reached yet (another thread's stream) stay pending
   for (int i = 0; i < g_prof.pending; ++i) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) != cudaSuccess) continue;
+    const cudaError_t e = cudaEventElapsedTime(&ms, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]);
+    if (e == cudaErrorNotReady) {
+      (void)cudaGetLastError();
+      std::swap(g_prof.ev[2 * keep], g_prof.ev[2 * i]);
+      std::swap(g_prof.ev[2 * keep + 1], g_prof.ev[2 * i + 1]);
+      g_prof.cls[keep] = g_prof.cls[i];
+      g_prof.bytes[keep] = g_prof.bytes[i];
+      g_prof.digit[keep] = g_prof.digit[i];
+      ++keep;
+      continue;
+    }
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
     int c = g_prof.cls[i];
     if (c == kKRadix && !((radix_live >> g_prof.digit[i]) & 1u)) c = kKRadixSkipped;
     g_prof.launches[c]++;
     g_prof.ms[c] += ms;
     g_prof.alg_bytes[c] += c == kKRadixSkipped ? 0.0 : g_prof.bytes[i];
   }
-  g_prof.pending = 0;
+  g_prof.pending = keep;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -445,7 +475,8 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   Ctrl* ctrl = (Ctrl*)(ws + pl.off_ctrl);
   const uint32_t max_attempts = p->max_attempts ? p->max_attempts : kDefaultAttempts;
   const uint32_t forced = (p->flags >> 8) & 0xFFu;
-  const bool trace = g_trace.buf != nullptr;
+  const Trace tr = trace_snapshot();
+  const bool trace = tr.buf != nullptr;
 
   // the comparison sort (stable merge) in place of the radix sort; its block-sorted runs start
   // in the buffer that leaves the last merge pass's output in d_out
@@ -477,7 +508,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     oa.L = pl.L;
     oa.seed = p->seed;
     oa.ctrl = ctrl;
-    oa.trace = g_trace;
+    oa.trace = tr;
   }
 
   RadixArgs ra{};
@@ -551,7 +582,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       a.seed = p->seed;
       a.ctrl = ctrl;
       a.ticket_slot = 0;
-      a.trace = g_trace;
+      a.trace = tr;
       const int mode = (first ? kModeFirst : 0) | (last ? kModeLast : 0);
       // algorithmic bytes: whole slot arrays in and out, the input and output records once
       const double slot_bytes = (double)pl.B * pl.Z * (pl.R + 4);
@@ -571,7 +602,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         ta.L = pl.L;
         ta.buf_tag = a.buf_in_tag;
         ta.seed = p->seed;
-        ta.trace = g_trace;
+        ta.trace = tr;
         const double tb = (double)pl.B * pl.Z * (2.0 + (first ? 0.0 : 4.0));  // rows out, tags in
         const int evt = prof_begin(st, kKPerm, tb);
         BOS_CUDA(launch_perm_table(ta, st, trace));
@@ -716,6 +747,7 @@ bos_status batch_build(const BatchIn& b, const BatchLayout& L, char* ws, const s
                        std::vector<char>* desc) {
   launches->clear();
   if (desc) desc->assign(L.desc_bytes, 0);
+  const Trace tr = trace_snapshot();  // the trace buffer the descriptors carry (debug)
   size_t dpos = 0;
   auto dev = [&](size_t pos) { return ws + L.desc_off + pos; };
   uint32_t ticket_slot = 0;
@@ -808,6 +840,11 @@ bos_status batch_build(const BatchIn& b, const BatchLayout& L, char* ws, const s
           pa.attempt = attempt[j];
           pa.seed = b.seeds[j];
           pa.ctrl = (Ctrl*)(ws + L.ctrl_off + (size_t)j * sizeof(Ctrl));
+          pa.trace = tr;
+          pa.buf_in_rec = src ? kBufRecB : kBufRecA;
+          pa.buf_in_tag = src ? kBufTagB : kBufTagA;
+          pa.buf_out_rec = dst ? kBufRecB : kBufRecA;
+          pa.buf_out_tag = dst ? kBufTagB : kBufTagA;
           const uint32_t sm = orp_smem_bytes(R, pa.Z, pa.k, last);
           smem = sm > smem ? sm : smem;
           if (desc) {
@@ -836,9 +873,10 @@ bos_status batch_build(const BatchIn& b, const BatchLayout& L, char* ws, const s
 
 bos_status batch_enqueue(const BatchLayout& L, char* ws, const std::vector<BatchLaunch>& launches, cudaStream_t st) {
   BOS_CUDA(cudaMemsetAsync(ws, 0, L.zero_end, st));
+  const bool trace = trace_snapshot().buf != nullptr;
   for (const BatchLaunch& l : launches) {
     if (l.kind == 0) {
-      BOS_CUDA(launch_orp_pass_batched(l.bp, l.mode, l.smem, st, L.R));
+      BOS_CUDA(launch_orp_pass_batched(l.bp, l.mode, l.smem, st, L.R, trace));
     } else {
       BOS_CUDA(launch_radix_batched(l.br, L.R, l.kind - 1, l.digit, st));
     }
@@ -1035,12 +1073,24 @@ bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t 
 }
 
 bos_status bos_trace_attach(void* d_buf, size_t bytes) {
+  std::lock_guard<std::mutex> g(g_state_mu);
   if (d_buf == nullptr) {
-    g_trace = Trace{nullptr, 0};
+    g_trace = Trace{nullptr, 0, 0};
     return BOS_OK;
   }
   if (((uintptr_t)d_buf & 15) || bytes < 32) return BOS_ERR_INVALID;
-  g_trace = Trace{(unsigned long long*)d_buf, (unsigned long long)(bytes / 16 - 1)};
+  g_trace = Trace{(unsigned long long*)d_buf, (unsigned long long)(bytes / 16 - 1), 0};
+  return BOS_OK;
+}
+
+bos_status bos_trace_attach_digest(void* d_buf, size_t bytes) {
+  std::lock_guard<std::mutex> g(g_state_mu);
+  if (d_buf == nullptr) {
+    g_trace = Trace{nullptr, 0, 0};
+    return BOS_OK;
+  }
+  if (((uintptr_t)d_buf & 15) || bytes < 256 * 16) return BOS_ERR_INVALID;
+  g_trace = Trace{(unsigned long long*)d_buf, 0, 1};
   return BOS_OK;
 }
 
@@ -1059,6 +1109,7 @@ const char* bos_status_str(bos_status s) {
 uint32_t bos_version(void) { return (0u << 16) | 1u; }
 
 bos_status bos_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(g_state_mu);
   if (on && !g_prof.created) {
     for (int i = 0; i < 2 * kMaxEv; ++i)
       if (cudaEventCreate(&g_prof.ev[i]) != cudaSuccess) {
@@ -1079,10 +1130,12 @@ bos_status bos_profile_enable(int on) {
 }
 
 uint32_t bos_profile_read(bos_kernel_stat* out, uint32_t max, uint64_t* total_launches) {
-  if (g_prof.pending) {  // bitonic calls do not synchronise: finish their events here
+  {  // bitonic calls do not synchronise: finish their events here
+    std::unique_lock<std::mutex> g(g_state_mu);
     for (int i = 0; i < g_prof.pending; ++i) cudaEventSynchronize(g_prof.ev[2 * i + 1]);
-    prof_collect(0xFFFFFFFFu);
   }
+  prof_collect(0xFFFFFFFFu);
+  std::lock_guard<std::mutex> g(g_state_mu);
   if (total_launches) *total_launches = g_prof.total_launches;
   uint32_t m = 0;
   for (int c = 0; c < kKCount && m < max; ++c) {

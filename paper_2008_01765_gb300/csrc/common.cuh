@@ -262,17 +262,38 @@ enum TraceBuf : uint32_t {
 enum TraceKind : uint32_t { kRead = 1, kWrite = 2 };
 
 struct Trace {
-  unsigned long long* buf;  // word 0 = entry counter; entries start at word 2
+  unsigned long long* buf;  // word 0 = entry counter; entries start at word 2 (digest: 256 slots)
   unsigned long long cap;   // entries that fit
+  uint32_t digest;          // 1: order-independent digest instead of the entries
 };
 
+// SplitMix64's output function (Steele, Lea, Flood 2014): a 64-bit mix for the trace digest.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Entry {(kind << 56) | (buffer << 48) | bytes, offset}. Digest mode: slot (SM id mod 256) of the
+// buffer counts the entries and sums mix64(word0 ^ mix64(offset)) modulo 2^64, so the sum over the
+// slots depends only on the multiset of entries, not on their order or on which SM logged them.
 template <bool TRACE>
 __device__ __forceinline__ void trace_log(const Trace& tr, uint32_t kind, uint32_t buffer,
                                           uint32_t bytes, uint64_t offset) {
   if constexpr (TRACE) {
+    if (tr.buf == nullptr) return;
+    const unsigned long long w0 = ((unsigned long long)kind << 56) | ((unsigned long long)buffer << 48) | bytes;
+    if (tr.digest) {
+      uint32_t smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      unsigned long long* slot = tr.buf + 2 * (smid & 255u);
+      atomicAdd(slot, 1ull);
+      atomicAdd(slot + 1, mix64(w0 ^ mix64(offset)));
+      return;
+    }
     const unsigned long long e = atomicAdd(tr.buf, 1ull);
     if (e < tr.cap) {
-      tr.buf[2 + 2 * e] = ((unsigned long long)kind << 56) | ((unsigned long long)buffer << 48) | bytes;
+      tr.buf[2 + 2 * e] = w0;
       tr.buf[3 + 2 * e] = offset;
     }
   }

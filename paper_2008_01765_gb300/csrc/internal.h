@@ -58,7 +58,8 @@ struct BatchPass {
   uint64_t nblocks;       // = first[narr]
   uint32_t* ticket;       // device: zeroed counter (LAST passes)
 };
-cudaError_t launch_orp_pass_batched(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st, int R);
+cudaError_t launch_orp_pass_batched(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st, int R,
+                                    bool trace);
 cudaError_t launch_orp_pass(const PassArgs& a, int mode, uint64_t grid, cudaStream_t st, int R,
                             bool trace);
 

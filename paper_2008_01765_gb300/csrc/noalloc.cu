@@ -2,45 +2,32 @@
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) at the point where they need a
 // permutation: code that runs inside a custom device allocator or its callbacks (allocating there
-// would re-enter the allocator), code that runs while a CUDA graph is being captured in relaxed or
-// global mode, real-time loops whose latency budget rules out an allocation that may synchronise
-// the device, and plugin hosts that own all device memory and forbid their guests to allocate.
-// bos_orp needs a workspace the caller allocates; this entry point uses instead a fixed scratch
-// array that is part of the library image, so the caller passes only its input and output.
+// would re-enter the allocator), and plugin hosts that own all device memory and forbid their
+// guests to allocate. bos_orp needs a workspace the caller allocates; this entry point uses
+// instead a fixed scratch array that is part of the library image, so the caller passes only its
+// input and output.
 //
 // The scratch is a file-scope __device__ array. Host code cannot use its name as an address (the
-// host-side symbol is only a stand-in), so the device address is looked up once per device with
-// cudaGetSymbolAddress and cached. The array is shared by every call on a device and keeps the
-// previous call's contents; the ORP clears its control block and look-back words itself at the
-// start of every attempt, and every other byte it reads was written earlier in the same call.
-#include <atomic>
-
+// host-side symbol is only a stand-in), so every call looks the device address up with
+// cudaGetSymbolAddress on the current device. That lookup is cheap and allocates nothing; looking
+// it up per call (not once per device) keeps the address right after a device reset or under
+// another context of the same device, where the module is loaded anew. The array is shared by
+// every call on a device and keeps the previous call's contents; the ORP clears its control
+// block and look-back words itself at the start of every attempt, and every other byte it reads
+// was written earlier in the same call.
 #include "bos.h"
 #include "internal.h"
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char g_scratch[BOS_NOALLOC_SCRATCH_BYTES];
 
-std::atomic<void*> g_scratch_addr[kMaxDevices];
-
-// Device address of g_scratch on the current device (looked up on the first call per device).
+// Device address of g_scratch on the current device.
 bos_status scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
     (void)cudaGetLastError();
     return BOS_ERR_CUDA;
-  }
-  if (dev < 0 || dev >= kMaxDevices) return BOS_ERR_INVALID;
-  void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
-  if (p == nullptr) {
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
-      (void)cudaGetLastError();
-      return BOS_ERR_CUDA;
-    }
-    g_scratch_addr[dev].store(p, std::memory_order_release);
   }
   *out = p;
   return BOS_OK;

@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) orp_pass_kernel(PassArgs a) {
 // Many arrays in one launch: block (or ticket) b is subproblem b - first[j] of array j, where
 // first[] holds the running sum of the arrays' subproblem counts. LAST passes take tickets over
 // the whole launch, so inside every array the subproblems start in order.
-template <int R, int MODE>
+template <int R, int MODE, bool TRACE>
 __global__ void __launch_bounds__(kThreads, 1) orp_pass_batched_kernel(BatchPass bp) {
   __shared__ unsigned long long q_s;
   __shared__ uint32_t j_s;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) orp_pass_batched_kernel(BatchPass
   }
   __syncthreads();
   const PassArgs a = bp.args[j_s];
-  orp_pass_body<R, MODE, false>(a, q_s);
+  orp_pass_body<R, MODE, TRACE>(a, q_s);
 }
 
 }  // namespace
@@ -386,31 +386,30 @@ static cudaError_t launch_r(const PassArgs& a, int mode, uint64_t grid, cudaStre
   }
 }
 
-template <int R, int MODE>
+template <int R, int MODE, bool TRACE>
 static cudaError_t batched_mode(const BatchPass& bp, uint32_t smem, cudaStream_t st) {
-  auto kern = orp_pass_batched_kernel<R, MODE>;
+  auto kern = orp_pass_batched_kernel<R, MODE, TRACE>;
   cudaError_t e = set_smem_optin(kern);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)bp.nblocks, kThreads, smem, st>>>(bp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_orp_pass_batched(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st, int R) {
-  if (bp.nblocks == 0) return cudaSuccess;
-  if (R == 8) {
-    switch (mode) {
-      case 0: return batched_mode<8, 0>(bp, smem, st);
-      case kModeFirst: return batched_mode<8, kModeFirst>(bp, smem, st);
-      case kModeLast: return batched_mode<8, kModeLast>(bp, smem, st);
-      default: return batched_mode<8, kModeFirst | kModeLast>(bp, smem, st);
-    }
-  }
+template <int R, bool TRACE>
+static cudaError_t batched_r(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st) {
   switch (mode) {
-    case 0: return batched_mode<16, 0>(bp, smem, st);
-    case kModeFirst: return batched_mode<16, kModeFirst>(bp, smem, st);
-    case kModeLast: return batched_mode<16, kModeLast>(bp, smem, st);
-    default: return batched_mode<16, kModeFirst | kModeLast>(bp, smem, st);
+    case 0: return batched_mode<R, 0, TRACE>(bp, smem, st);
+    case kModeFirst: return batched_mode<R, kModeFirst, TRACE>(bp, smem, st);
+    case kModeLast: return batched_mode<R, kModeLast, TRACE>(bp, smem, st);
+    default: return batched_mode<R, kModeFirst | kModeLast, TRACE>(bp, smem, st);
   }
+}
+
+cudaError_t launch_orp_pass_batched(const BatchPass& bp, int mode, uint32_t smem, cudaStream_t st, int R,
+                                    bool trace) {
+  if (bp.nblocks == 0) return cudaSuccess;
+  if (R == 8) return trace ? batched_r<8, true>(bp, mode, smem, st) : batched_r<8, false>(bp, mode, smem, st);
+  return trace ? batched_r<16, true>(bp, mode, smem, st) : batched_r<16, false>(bp, mode, smem, st);
 }
 
 cudaError_t launch_orp_pass(const PassArgs& a, int mode, uint64_t grid, cudaStream_t st, int R, bool trace) {

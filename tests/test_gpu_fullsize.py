@@ -113,6 +113,33 @@ def test_address_trace_2p20_identical_across_inputs(bos):
         np.testing.assert_array_equal(_trace_digest(bos, inputs.make_records(n, 16, dist, seed=3), Z, 9), base)
 
 
+@pytest.mark.parametrize("dist", ["equal", "reverse"])
+def test_trace_digest_2p30_identical_across_inputs(bos, big, dist):
+    # The full n = 2^30 benchmark ORP, in bench.py's plan, through the order-independent trace
+    # digest (count and sum of a 64-bit mix of every global access, Section 3.1): uniform,
+    # all-equal and reverse-sorted keys give the same digest for one seed.
+    import torch
+
+    def digest(d):
+        recs = inputs.make_records(N30, 16, d, seed=1)
+        big["x"].copy_(torch.from_numpy(recs.view(np.uint8)))
+        buf = torch.zeros(256 * 16, dtype=torch.uint8, device="cuda")
+        bos.trace_attach_digest(buf)
+        try:
+            bos.orp(big["x"], 16, Z=Z30, seed=7, out=big["out"], workspace=big["ws"])
+            torch.cuda.synchronize()
+        finally:
+            bos.trace_attach_digest(None)
+        w = buf.view(torch.int64).cpu().numpy().view(np.uint64).reshape(256, 2)
+        return int(w[:, 0].sum()), int(w[:, 1].sum(dtype=np.uint64))
+
+    if "digest_uniform" not in big:
+        big["digest_uniform"] = digest("uniform")
+    cnt, h = big["digest_uniform"]
+    assert cnt > 2 * N30  # every slot of the first pass's output and the LAST pass's input, at least
+    assert digest(dist) == (cnt, h)
+
+
 def test_batched_4096_arrays_sampled(bos):
     # The benchmark's batch (4096 arrays, sizes log-uniform in [2^10, 2^20], Z per size class),
     # run as one launch sequence; 24 arrays are checked against the oracle run alone.

@@ -509,3 +509,63 @@ def test_stream_trace_is_input_and_seed_independent(bos):
     B = 1 << 11
     wr_tag = base[(kind_buf(base) == 2) & ((base[:, 0] >> np.uint64(56)) == 2)]
     assert len(wr_tag) >= B * Z // 8
+
+
+def _kind_buf(t):
+    return (t[:, 0] >> np.uint64(48)) & np.uint64(0xFF)
+
+
+def test_address_trace_cfg1_plain_form(bos):
+    # Config 1's shape: n = 2^16 8-byte records, Z = 512 (B = 256), the plain form (one level per
+    # launch). The multiset of global accesses is the same for every input (Section 3.1), and for
+    # every seed but the compacted output writes (their addresses follow the final loads, Lemma 3.3).
+    n, Z = 1 << 16, 512
+    base = None
+    for dist in ("uniform", "equal", "sorted", "reverse"):
+        t = _trace(bos, inputs.make_records(n, 8, dist, seed=12), Z, seed=1, k=1)
+        if base is None:
+            base = t
+        else:
+            np.testing.assert_array_equal(t, base)
+    t2 = _trace(bos, inputs.make_records(n, 8, "uniform", seed=12), Z, seed=77, k=1)
+    np.testing.assert_array_equal(t2[_kind_buf(t2) != 5], base[_kind_buf(base) != 5])
+    # eight passes, each reading and writing every slot of both slot arrays in turn
+    assert int((_kind_buf(base) != 5).sum()) > 0
+
+
+def _batch_trace(bos, sizes, rec_bytes, dist, seeds, Zs, ops):
+    import torch
+    recs, offs = inputs.make_batch(sizes, rec_bytes, seed=5)
+    if dist == "equal":
+        recs["key"] = 0x55
+    elif dist == "reverse":
+        recs["key"] = np.arange(recs.size, 0, -1, dtype=recs["key"].dtype)
+    x = bos.to_device(recs)
+    out = torch.empty_like(x)
+    buf = torch.zeros(1 << 26, dtype=torch.uint8, device="cuda")
+    bos.trace_attach(buf)
+    try:
+        bos.sort_batched(x, out, offs, seeds, ops, bos.params(rec_bytes, 512, 0), Zs=Zs)
+        torch.cuda.synchronize()
+    finally:
+        bos.trace_attach(None)
+    w = buf.view(torch.int64).cpu().numpy().view(np.uint64)
+    cnt = int(w[0])
+    assert 0 < cnt <= buf.numel() // 16 - 1
+    ent = w[2:2 + 2 * cnt].reshape(cnt, 2)
+    return ent[np.lexsort((ent[:, 1], ent[:, 0]))]
+
+
+def test_batched_kernel_trace_is_input_independent(bos):
+    # The batched (one-CTA-per-subproblem) kernel that the batched and serving workloads run, on a
+    # mixed batch: uneven sizes, two bucket sizes, ORP and sort arrays. Its ORP accesses are the
+    # same multiset for every input content, and for other seeds except the compacted writes.
+    sizes = np.array([1024, 3000, 4096, 777, 12000, 20000, 1, 0, 65536, 5000], dtype=np.int64)
+    Zs = np.where(np.arange(sizes.size) % 2 == 0, 512, 64).astype(np.uint32)
+    ops = (np.arange(sizes.size) % 3 == 0).astype(np.uint8)
+    seeds = np.arange(7, 7 + sizes.size, dtype=np.uint64)
+    base = _batch_trace(bos, sizes, 8, "uniform", seeds, Zs, ops)
+    for dist in ("equal", "reverse"):
+        np.testing.assert_array_equal(_batch_trace(bos, sizes, 8, dist, seeds, Zs, ops), base)
+    t2 = _batch_trace(bos, sizes, 8, "uniform", seeds + np.uint64(1000), Zs, ops)
+    np.testing.assert_array_equal(t2[_kind_buf(t2) != 5], base[_kind_buf(base) != 5])
