@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="bos_params.flags (comparisons)")
     ap.add_argument("--k", type=int, default=0, help="levels per ORP pass (0 = automatic)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ORP-by-distribution timings and the batched and serving summaries")
     ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving"],
                     help="sort: n=2^30 16-B records (the headline); batched: 4096 arrays of 2^10..2^20 "
                          "8-B records in one CUDA graph; serving: a Poisson request stream")
@@ -163,20 +165,33 @@ def traffic_for(kernel, workload):
     return None
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(n_log2, Z, dist):
-    """The oracle (literal Algorithm 3.1 + in-bin permutation + std::stable_sort), one thread,
-    on a bounded sample of the workload."""
+    """The oracle (literal Algorithm 3.1 + in-bin permutation + LSD radix sort) on a bounded
+    sample of the workload: on all the host's cores (its threaded build: each step's independent
+    work split across std::threads) and on one thread."""
     import oracle
     from paper_2008_01765_gb300 import inputs
     n = 1 << n_log2
     recs = inputs.make_records(n, REC, dist, seed=1)
     oracle.lib()
+    cores = host_cores()
     t0 = time.perf_counter()
-    oracle.sort(recs, Z, 1, method=oracle.LITERAL)
+    oracle.sort_threads(recs, Z, 1, cores)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"n=2^{n_log2} 16-B records ({dist} u64 keys), Z={Z}, literal Algorithm 3.1 + "
-                      f"in-bin permutation + std::stable_sort, one host thread, {dt:.2f} s"}
+    t0 = time.perf_counter()
+    oracle.sort(recs, Z, 1, method=oracle.LITERAL, sorter=1)
+    dt1 = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"n=2^{n_log2} 16-B records ({dist} u64 keys), Z={Z}, literal Algorithm 3.1 + in-bin "
+                      f"permutation + LSD radix sort, {cores} host threads (nproc = {cores}), {dt:.2f} s",
+            "one_thread": {"value": n / dt1, "unit": UNIT, "seconds": dt1}}
 
 
 def run_reference(args):
@@ -188,22 +203,23 @@ def run_reference(args):
     n = 1 << args.cpu_sample_log2
     recs = inputs.make_records(n, REC, args.dist, seed=1)
     oracle.lib()
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle.sort(recs, args.Z, 1, method=oracle.LITERAL)
+        oracle.sort_threads(recs, args.Z, 1, cores)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        oracle.sort(recs, args.Z, 1 + s, method=oracle.LITERAL)
+        oracle.sort_threads(recs, args.Z, 1 + s, cores)
     dt = (time.perf_counter() - t0) / args.steps
     v = n / dt
     sample = (f"each step: n=2^{args.cpu_sample_log2} 16-B records ({args.dist} u64 keys), Z={args.Z}, "
-              f"oracle (literal Algorithm 3.1 + in-bin permutation + std::stable_sort), one host thread")
+              f"oracle (literal Algorithm 3.1 + in-bin permutation + LSD radix sort), {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"sort n=2^{args.n_log2} rec16 Z={args.Z}", "n": 1 << args.n_log2,
                        "rec_bytes": REC, "Z": args.Z, "keys": f"{args.dist} u64, payload = index",
-                       "sample_n": n, "parallelism": "one host thread"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                       "sample_n": n, "parallelism": f"{cores} host threads"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -232,10 +248,18 @@ def run_batched(args):
     import torch
     from paper_2008_01765_gb300 import _build
     _build.build()
-    from paper_2008_01765_gb300 import autotune, bos, inputs
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    line = batched_measure(args, torch.device("cuda", local), world, rank, pg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def batched_measure(args, dev, world=1, rank=0, pg=None):
+    """The batched workload: 4096 arrays of 2^10..2^20 8-byte records in one CUDA graph."""
+    import torch
+    from paper_2008_01765_gb300 import autotune, bos, inputs
+    local = dev.index
     sizes = inputs.batched_sizes(4096, 10.0, 20.0, seed=1 + rank)
     recs, offs = inputs.make_batch(sizes, 8, seed=1 + rank)
     Zs = autotune.z_array(sizes, 8)
@@ -301,23 +325,26 @@ def run_batched(args):
         ems = e0.elapsed_time(e1) / k
         line["e2e"] = {"value": world * n_total / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n_total * 8,
                        "d2h_bytes_per_step": n_total * 8, "ms_per_step": ems}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serving(args):
     """Poisson stream of ORP and sort requests (50/50), n log-uniform in [2^12, 2^26], 16-B
     records {u64 key uniform, u64 payload}, 64 GiB admission budget. The arrival rate is 70% of
     the capacity measured by a burst of the same requests first."""
-    import threading
     import torch
     from paper_2008_01765_gb300 import _build
     _build.build()
-    from paper_2008_01765_gb300 import inputs, serve
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
+    line = serving_measure(args, local, world, rank, max(40, args.steps * 40))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_measure(args, local, world=1, rank=0, count=40):
+    from paper_2008_01765_gb300 import inputs, serve
     pool = inputs.make_records(1 << 26, 16, "uniform", seed=7 + rank, payload="random")
-    count = max(40, args.steps * 40)
     arrivals, sizes, ops, seeds = inputs.poisson_stream(count, 1.0, 12.0, 26.0, seed=3 + rank)
     rng = np.random.default_rng(5 + rank)
     offs = [int(rng.integers(0, pool.size - n + 1)) for n in sizes]
@@ -373,8 +400,7 @@ def run_serving(args):
                        "capacity_records_per_s": sum(int(n) for n in sizes) / (t1 - t0),
                        "batched_requests": st["batched_requests"], "peak_held_bytes": st["peak_held_bytes"]},
             "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -458,6 +484,37 @@ def main():
             "roofline": roof, "kernels": kernels, "gpu_launches": launches,
             "clocks": clk}
 
+    # ---- the ORP alone (Algorithm 3.1 + Section 3.2) on uniform, all-equal and reverse-sorted
+    # keys: its time does not depend on the data. Inputs are made on the device (x is refilled from
+    # the host by the end-to-end leg below). ----
+    if not args.no_extras:
+        ws_orp = ws
+        by_dist = {}
+        xv = x.view(torch.int64).view(n, 2)
+        for dist in ("uniform", "equal", "reverse"):
+            if dist == "equal":
+                xv[:, 0] = 0x5555555555555555
+            elif dist == "reverse":
+                xv[:, 0] = torch.arange(n - 1, -1, -1, dtype=torch.int64, device=dev)
+            if dist != "uniform":
+                xv[:, 1] = torch.arange(n, dtype=torch.int64, device=dev)
+            p.seed, p.k = 4000, args.k
+            bos.orp_raw(x.data_ptr(), out.data_ptr(), n, p, ws_orp.data_ptr(), ws_orp.numel(), sh)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for s2 in range(2):
+                p.seed = 1 + s2
+                oinfo = bos.orp_raw(x.data_ptr(), out.data_ptr(), n, p, ws_orp.data_ptr(), ws_orp.numel(), sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            by_dist[dist] = {"ms": e0.elapsed_time(e1) / 2, "attempts": int(oinfo.attempts)}
+        t = [v["ms"] for v in by_dist.values()]
+        line["orp_by_dist"] = dict(by_dist, spread=(max(t) - min(t)) / min(t),
+                                   note="bos_orp alone at the benchmark size, seeds 1-2 each")
+        del ws_orp
+        if args.no_e2e:  # the end-to-end leg would refill x from the host
+            x.copy_(host_in)
+
     # ---- end to end through the public API with host buffers (H2D + sort + D2H every step) ----
     # A stream of sorts from pinned host memory: every step copies its input in and reads its
     # result back inside the timed region. Buffers are doubled so that the copy of step s+1's
@@ -468,32 +525,49 @@ def main():
         xin, xo = [x, torch.empty_like(x)], [out, torch.empty_like(out)]
         h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
+        def tev():
+            return torch.cuda.Event(enable_timing=True)
+
+        spans = {"h2d": [], "sort": [], "d2h": []}
+
         def e2e_run(ke, seed0, start=None):
+            spans["h2d"].clear(), spans["sort"].clear(), spans["d2h"].clear()
             if start is not None:
                 h2d.wait_event(start)
-            ev_in = [torch.cuda.Event() for _ in range(ke)]
+            ev_in = [None] * ke
             ev_out = [None, None]
-            with torch.cuda.stream(h2d):
-                xin[0].copy_(pin_in, non_blocking=True)
-                ev_in[0].record(h2d)
+
+            def copy_in(s):
+                b0, b1 = tev(), tev()
+                with torch.cuda.stream(h2d):
+                    b0.record(h2d)
+                    xin[s % 2].copy_(pin_in, non_blocking=True)
+                    b1.record(h2d)
+                spans["h2d"].append((b0, b1))
+                ev_in[s] = b1
+
+            copy_in(0)
             for s in range(ke):
                 b = s % 2
                 if s + 1 < ke:  # xin[1 - b] was last read by sort s - 1, which has returned
-                    with torch.cuda.stream(h2d):
-                        xin[1 - b].copy_(pin_in, non_blocking=True)
-                        ev_in[s + 1].record(h2d)
+                    copy_in(s + 1)
                 stream.wait_event(ev_in[s])
                 if ev_out[b] is not None:
                     stream.wait_event(ev_out[b])
                 p.seed, p.k = seed0 + s, args.k
+                s0, s1 = tev(), tev()
+                s0.record(stream)
                 bos.sort_raw(xin[b].data_ptr(), xo[b].data_ptr(), n, p, ws.data_ptr(), ws.numel(), sh)
-                done = torch.cuda.Event()
-                done.record(stream)
+                s1.record(stream)
+                spans["sort"].append((s0, s1))
                 with torch.cuda.stream(d2h):
-                    d2h.wait_event(done)
+                    d2h.wait_event(s1)
+                    d0, d1 = tev(), tev()
+                    d0.record(d2h)
                     pin_out.copy_(xo[b], non_blocking=True)
-                    ev_out[b] = torch.cuda.Event()
-                    ev_out[b].record(d2h)
+                    d1.record(d2h)
+                    ev_out[b] = d1
+                spans["d2h"].append((d0, d1))
             stream.wait_stream(h2d)
             stream.wait_stream(d2h)
 
@@ -506,9 +580,17 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(pg, e0.elapsed_time(e1) / ke, dev)
+        avg = {k: float(np.mean([a.elapsed_time(b) for a, b in v])) for k, v in spans.items()}
+        # start and end of every copy and sort of the first three steps, ms after the timed start
+        timeline = {k: [[round(e0.elapsed_time(a), 1), round(e0.elapsed_time(b), 1)] for a, b in v[:3]]
+                    for k, v in spans.items()}
         line["e2e"] = {"value": world * n / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * REC,
                        "d2h_bytes_per_step": n * REC, "ms_per_step": ems, "steps": ke,
-                       "pipeline": "double buffers: H2D of step s+1 and D2H of step s-1 on copy streams during sort s"}
+                       "h2d_ms": avg["h2d"], "d2h_ms": avg["d2h"], "sort_ms": avg["sort"],
+                       "h2d_GBps": n * REC / (avg["h2d"] / 1e3) / 1e9, "d2h_GBps": n * REC / (avg["d2h"] / 1e3) / 1e9,
+                       "timeline_ms": timeline,
+                       "pipeline": "double buffers: H2D of step s+1 and D2H of step s-1 on copy streams during sort s; "
+                                   "per-stream times are CUDA events around each copy and each bos_sort"}
         del pin_in, pin_out, xin, xo
 
     # ---- comparators: plain one-level-per-launch form, GPU bitonic sort (rank-local) ----
@@ -550,6 +632,27 @@ def main():
         line["comparators"] = comp
         line["speedup_vs_plain"] = pms / ms
         line["speedup_vs_bitonic"] = bms / ms
+
+    # ---- the batched and serving workloads, summarised beside the headline ----
+    if not args.no_extras and world == 1:
+        del x, out  # the headline's buffers (its workspace went before the bitonic comparator)
+        torch.cuda.empty_cache()
+        try:
+            bl = batched_measure(args, dev)
+            line["batched"] = {"records_per_s": bl["value"], "ms_per_step": bl["ms_per_step"],
+                               "hbm_gbs": bl["hbm_gbs"], "hbm_frac": bl["hbm_frac"],
+                               "arrays": bl["config"]["arrays"], "records": bl["config"]["records"],
+                               "e2e_records_per_s": bl.get("e2e", {}).get("value")}
+        except Exception as ex:  # pragma: no cover
+            line["batched"] = {"error": str(ex)}
+        torch.cuda.empty_cache()
+        try:
+            sl = serving_measure(args, local, count=40)
+            line["serving"] = {"records_per_s": sl["value"], "p50_ms": sl["p50_ms"], "p99_ms": sl["p99_ms"],
+                               "requests": sl["config"]["requests"],
+                               "arrival_rate_per_s": sl["config"]["arrival_rate_per_s"]}
+        except Exception as ex:  # pragma: no cover
+            line["serving"] = {"error": str(ex)}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         try:

@@ -55,6 +55,9 @@ def lib():
         L.or_sort.argtypes = [_vp, _vp, _u64, _u32, _u32, _u32, _u64, _u32, ctypes.c_int,
                               ctypes.c_int, ctypes.POINTER(OrpInfo)]
         L.or_sort.restype = ctypes.c_int
+        L.or_sort_threads.argtypes = [_vp, _vp, _u64, _u32, _u32, _u32, _u64, _u32, _u32,
+                                      ctypes.POINTER(OrpInfo)]
+        L.or_sort_threads.restype = ctypes.c_int
         L.or_orp_sample.argtypes = [_u64, _u32, _u64, _u32, _vp, _u32, _vp, _vp, _vp, _u64]
         L.or_orp_sample.restype = ctypes.c_int
         L.or_bitonic_sort.argtypes = [_vp, _u64, _u32, _u32]
@@ -208,6 +211,19 @@ def sort(recs, Z, seed, max_attempts=8, method=LITERAL, sorter=0, first_attempt=
     info = OrpInfo()
     st = lib().or_sort(_ptr(recs), _ptr(out), recs.shape[0], _rec_bytes(recs), _key_bytes(recs),
                        Z, seed, max_attempts, method, sorter, ctypes.byref(info))
+    if st != OK:
+        raise OracleError(st)
+    return out, info
+
+
+def sort_threads(recs, Z, seed, threads, max_attempts=8):
+    """or_sort (literal ORP + LSD radix) with each step split across `threads` host threads:
+    the threaded CPU baseline. Returns (out, info)."""
+    recs = np.ascontiguousarray(recs)
+    out = np.zeros_like(recs)
+    info = OrpInfo()
+    st = lib().or_sort_threads(_ptr(recs), _ptr(out), recs.shape[0], _rec_bytes(recs), _key_bytes(recs),
+                               Z, seed, max_attempts, threads, ctypes.byref(info))
     if st != OK:
         raise OracleError(st)
     return out, info

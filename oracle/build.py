@@ -15,7 +15,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-std=c++17", "-O2", "-shared", "-fPIC", "-o", tmp, SRC]
+    cmd = ["g++", "-std=c++17", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

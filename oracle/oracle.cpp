@@ -1,7 +1,7 @@
 // Oracle for bucket oblivious random permutation (ORP) and bucket oblivious sort.
 //
-// TEST INFRASTRUCTURE ONLY. This file is a plain, slow, single-threaded C++17 restatement of
-// what the method computes, written from the paper (Asharov, Chan, Nayak, Pass, Ren, Shi,
+// TEST INFRASTRUCTURE ONLY. This file is a plain, slow C++17 restatement of what the method
+// computes, written from the paper (Asharov, Chan, Nayak, Pass, Ren, Shi,
 // "Bucket Oblivious Sort: An Extremely Simple Oblivious Sort", SOSA 2020). Only the tests, the
 // package's smoke check and the benchmark's CPU-baseline leg may load it. It shares no code,
 // header, table or helper with the CUDA library; the two meet only through seeded inputs.
@@ -11,6 +11,9 @@
 // the overflow test against its closed form and the binomial bounds of Lemma 3.2, the ORP
 // against uniformity over all permutations (Lemma 3.3), the access count against Section 3.4,
 // the sort against std::stable_sort / an LSD radix sort, the bitonic network against std::sort.
+// Everything runs on one thread except or_sort_threads, the same literal algorithm with the
+// independent work of each step split across std::threads (the threaded CPU baseline), which is
+// pinned equal to the one-thread or_sort.
 //
 // Conventions (the paper leaves them open; each reading is listed in the design notes):
 //   * B is the smallest power of two with B*Z >= 2n (Algorithm 3.1), L = log2 B.
@@ -24,8 +27,10 @@
 //   * Overflow ("more than Z" reals in a MergeSplit output) aborts the attempt; the next attempt
 //     uses attempt+1 in every Philox counter.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -278,6 +283,116 @@ uint64_t payload_of(const uint8_t* rec, uint32_t rec_bytes, uint32_t key_bytes) 
   return p;
 }
 
+// Runs f(lo, hi) on `threads` std::threads over contiguous ranges of [0, count).
+template <typename F>
+void parallel_ranges(uint64_t count, uint32_t threads, F f) {
+  if (threads <= 1 || count < 2) {
+    f(0, count);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (uint32_t t = 0; t < threads; ++t) {
+    const uint64_t lo = count * t / threads, hi = count * (t + 1) / threads;
+    if (lo < hi) pool.emplace_back(f, lo, hi);
+  }
+  for (auto& th : pool) th.join();
+}
+
+// Literal Algorithm 3.1 as bin_assignment_literal, with the placement of the groups and the
+// B/2 MergeSplits of every level (independent of one another) split across threads.
+bool bin_assignment_literal_mt(uint64_t n, uint32_t Z, uint64_t seed, uint32_t attempt,
+                               std::vector<Slot>* final_buckets, uint32_t threads) {
+  uint64_t B;
+  uint32_t L;
+  geometry(n, Z, &B, &L);
+  std::vector<Slot> cur(B * Z), nxt(B * Z);
+  parallel_ranges(B, threads, [&](uint64_t j0, uint64_t j1) {
+    for (uint64_t j = j0; j < j1; ++j) {
+      const uint64_t lo = group_lo(j, n, B), hi = group_lo(j + 1, n, B);
+      for (uint32_t s = 0; s < Z; ++s)
+        cur[j * Z + s] = lo + s < hi ? Slot{true, label_of(lo + s, seed, attempt, L), lo + s} : Slot{false, 0, 0};
+    }
+  });
+  for (uint32_t i = 0; i < L; ++i) {
+    const uint32_t bit = L - 1 - i;
+    std::atomic<bool> failed{false};
+    parallel_ranges(B / 2, threads, [&](uint64_t j0, uint64_t j1) {
+      Counters cnt;
+      for (uint64_t j = j0; j < j1 && !failed.load(std::memory_order_relaxed); ++j) {
+        const uint64_t jp = (j >> i) << i;
+        const uint64_t a = jp + j, b = jp + j + (1ull << i);
+        if (!merge_split(&cur[a * Z], &cur[b * Z], &nxt[(2 * j) * Z], &nxt[(2 * j + 1) * Z], Z, bit,
+                         &cnt, nullptr, i, a, b, 2 * j, 2 * j + 1))
+          failed.store(true);
+      }
+    });
+    if (failed.load()) return false;
+    std::swap(cur, nxt);
+  }
+  *final_buckets = std::move(cur);
+  return true;
+}
+
+// permute_and_strip with the buckets split across threads (offsets from the loads first).
+void permute_and_strip_mt(const std::vector<Slot>& fin, uint64_t B, uint32_t Z, uint64_t seed,
+                          uint32_t attempt, const uint8_t* in, uint8_t* out, uint32_t rec_bytes,
+                          uint32_t threads) {
+  std::vector<uint64_t> start(B + 1, 0);
+  for (uint64_t b = 0; b < B; ++b) {
+    uint32_t m = 0;
+    while (m < Z && fin[b * Z + m].real) ++m;
+    start[b + 1] = start[b] + m;
+  }
+  parallel_ranges(B, threads, [&](uint64_t b0, uint64_t b1) {
+    for (uint64_t b = b0; b < b1; ++b) {
+      const uint32_t m = (uint32_t)(start[b + 1] - start[b]);
+      std::vector<std::pair<uint64_t, uint32_t>> keyed(m);
+      for (uint32_t s = 0; s < m; ++s) {
+        uint32_t w[4];
+        philox_at(b * Z + s, attempt, 1, seed, w);
+        keyed[s] = {((uint64_t)w[0] << 32) | w[1], s};
+      }
+      std::sort(keyed.begin(), keyed.end());
+      for (uint32_t j = 0; j < m; ++j)
+        std::memcpy(out + (start[b] + j) * rec_bytes, in + fin[b * Z + keyed[j].second].src * rec_bytes, rec_bytes);
+    }
+  });
+}
+
+// Stable LSD radix sort on 8-bit digits with each pass split across threads: every thread
+// counts its contiguous range, the offsets are the per-digit prefix over (digit, thread), and
+// every thread scatters its range in order (so equal digits keep their order).
+void radix_sort_mt(uint8_t* r, uint64_t n, uint32_t rec_bytes, uint32_t key_bytes, uint32_t threads) {
+  if (threads < 1) threads = 1;
+  std::vector<uint8_t> tmp(n * rec_bytes);
+  uint8_t* src = r;
+  uint8_t* dst = tmp.data();
+  std::vector<uint64_t> cnt((size_t)threads * 256);
+  for (uint32_t d = 0; d < key_bytes; ++d) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    parallel_ranges(threads, threads, [&](uint64_t t0, uint64_t t1) {
+      for (uint64_t t = t0; t < t1; ++t)
+        for (uint64_t i = n * t / threads; i < n * (t + 1) / threads; ++i) cnt[t * 256 + src[i * rec_bytes + d]]++;
+    });
+    uint64_t run = 0;
+    for (int v = 0; v < 256; ++v)
+      for (uint32_t t = 0; t < threads; ++t) {
+        const uint64_t c = cnt[(size_t)t * 256 + v];
+        cnt[(size_t)t * 256 + v] = run;
+        run += c;
+      }
+    parallel_ranges(threads, threads, [&](uint64_t t0, uint64_t t1) {
+      for (uint64_t t = t0; t < t1; ++t)
+        for (uint64_t i = n * t / threads; i < n * (t + 1) / threads; ++i) {
+          const uint8_t v = src[i * rec_bytes + d];
+          std::memcpy(dst + (cnt[t * 256 + v]++) * rec_bytes, src + i * rec_bytes, rec_bytes);
+        }
+    });
+    std::swap(src, dst);
+  }
+  if (src != r) std::memcpy(r, src, n * rec_bytes);
+}
+
 struct OrpInfo {
   uint32_t attempts;
   uint32_t L;
@@ -490,6 +605,36 @@ int or_sort(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t 
   else
     or_stable_sort(out, n, rec_bytes, key_bytes);
   return OR_OK;
+}
+
+// or_sort (literal ORP, then the LSD radix sort) with the work of each step split across
+// `threads` std::threads: the threaded CPU baseline. Same output as or_sort(method 0, sorter 1).
+int or_sort_threads(const void* in, void* out, uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                    uint32_t Z, uint64_t seed, uint32_t max_attempts, uint32_t threads, OrpInfo* info) {
+  if (key_bytes != 4 && key_bytes != 8) return OR_ERR_INVALID;
+  if (key_bytes >= rec_bytes || (rec_bytes != 8 && rec_bytes != 16) || Z < 1 || max_attempts < 1)
+    return OR_ERR_INVALID;
+  uint64_t B;
+  uint32_t L;
+  geometry(n, Z, &B, &L);
+  if (info) {
+    info->B = B;
+    info->L = L;
+  }
+  for (uint32_t a = 0; a < max_attempts; ++a) {
+    std::vector<Slot> fin;
+    if (!bin_assignment_literal_mt(n, Z, seed, a, &fin, threads)) continue;
+    permute_and_strip_mt(fin, B, Z, seed, a, (const uint8_t*)in, (uint8_t*)out, rec_bytes, threads);
+    radix_sort_mt((uint8_t*)out, n, rec_bytes, key_bytes, threads);
+    if (info) {
+      info->attempts = a + 1;
+      info->slot_reads = 2ull * B * Z * L;
+      info->slot_writes = 2ull * B * Z * L;
+    }
+    return OR_OK;
+  }
+  if (info) info->attempts = max_attempts;
+  return OR_ERR_OVERFLOW;
 }
 
 // Bitonic sorting network (Batcher 1968; the comparator of Table 1) on n = 2^m records,

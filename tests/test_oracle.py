@@ -426,3 +426,24 @@ def test_orp_sample_equals_full_orp():
     for b in buckets:
         seg = out["payload"][int(off[b]):int(off[b]) + int(load[b])]
         np.testing.assert_array_equal(seg, src[b])
+
+
+@pytest.mark.parametrize("n,Z,rec_bytes,dist", [(0, 4, 8, "uniform"), (5, 2, 16, "uniform"), (3001, 16, 8, "dup1024"), (3001, 8, 8, "uniform"),
+                                                (20000, 64, 16, "uniform"), (65536, 512, 8, "reverse")])
+def test_threaded_baseline_equals_one_thread(n, Z, rec_bytes, dist):
+    # The threaded CPU baseline is the same literal algorithm (Algorithm 3.1, Section 3.2, an LSD
+    # radix sort as Section 3.3's sort) with each step's independent work split across threads:
+    # its output and attempt count equal the one-thread oracle's for every thread count.
+    recs = inputs.make_records(n, rec_bytes, dist, seed=n + 1)
+    for seed in (1, 9):
+        try:
+            ref, ri = oracle.sort(recs, Z, seed, max_attempts=32, method=oracle.LITERAL, sorter=1)
+        except oracle.OracleError as e:  # every attempt overflows: so must the threaded run
+            assert e.status == oracle.ERR_OVERFLOW
+            with pytest.raises(oracle.OracleError):
+                oracle.sort_threads(recs, Z, seed, 4, max_attempts=32)
+            continue
+        for threads in (1, 3, 8):
+            got, gi = oracle.sort_threads(recs, Z, seed, threads, max_attempts=32)
+            assert gi.attempts == ri.attempts
+            np.testing.assert_array_equal(got, ref)
