@@ -220,6 +220,16 @@ def bitonic_sort(x, rec_bytes, out=None, stream=None):
     return out
 
 
+def batched_workspace_bytes(offsets, Zs, ops, base: Params) -> int:
+    """bos_batched_workspace_bytes for host arrays (offsets num + 1, Zs or None, ops)."""
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    ops = np.ascontiguousarray(ops, dtype=np.uint8)
+    Zs = None if Zs is None else np.ascontiguousarray(Zs, dtype=np.uint32)
+    return int(lib().bos_batched_workspace_bytes(off.ctypes.data_as(_vp), off.size - 1,
+                                                 None if Zs is None else Zs.ctypes.data_as(_vp),
+                                                 ops.ctypes.data_as(_vp), ctypes.byref(base)))
+
+
 class Batch:
     """A batch of back-to-back arrays (bos_sort_batched and its prepare/enqueue/collect steps).
 

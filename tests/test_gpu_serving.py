@@ -1,5 +1,9 @@
 """Serving loop on the GPU: requests that run together (overlapping on several streams, small
-ones merged into batched launches) give exactly the result they give alone."""
+ones merged into batched launches) give exactly the result they give alone.
+
+Two mixes: many small requests (n in [2^8, 2^19], a 2 GiB budget, so admission waits and small
+requests share batched launches), and the serving workload's own sizes (n log-uniform in
+[2^12, 2^26] 16-byte records under a 64 GiB budget, 50/50 ORP and sort)."""
 import numpy as np
 import pytest
 
@@ -40,3 +44,45 @@ def test_results_same_alone_and_in_the_mix(bos):
         assert r.attempts == rinfo.attempts
     st = srv.stats()
     assert st["requests"] == len(jobs)
+
+
+def test_serving_sizes_2p12_to_2p26_same_alone_and_in_the_mix(bos):
+    # Every result equals the same request run alone; up to 2^20 records it equals the oracle's
+    # closed form too; above, an ORP result is checked on sampled final buckets (oracle, bucket by
+    # bucket) and a sort result is the stable sort of the ORP output run alone.
+    import torch
+    from paper_2008_01765_gb300 import serve
+    rng = np.random.default_rng(11)
+    sizes = np.floor(np.exp2(rng.uniform(12, 26, size=24))).astype(int)
+    sizes[0], sizes[1] = 1 << 26, 1 << 12
+    jobs = [(inputs.make_records(int(n), 16, "uniform", seed=50 + j, payload="random"), int(j % 2), 2000 + j)
+            for j, n in enumerate(sizes)]
+    srv = serve.Server(budget_bytes=64 << 30, workers=4, rec_bytes=16, small_max=1 << 14, max_batch=16)
+    reqs = [srv.submit(recs, op=op, seed=seed) for recs, op, seed in jobs]
+    got = [r.wait(900) for r in reqs]
+    srv.close()
+    st = srv.stats()
+    assert st["requests"] == len(jobs) and st["peak_held_bytes"] <= 64 << 30
+    for (recs, op, seed), r, out in zip(jobs, reqs, got):
+        n = recs.shape[0]
+        x = bos.to_device(recs)
+        alone, info = (bos.sort if op else bos.orp)(x, 16, Z=r.Z, seed=seed)
+        np.testing.assert_array_equal(out, bos.to_host(alone, recs.dtype))
+        assert r.attempts == info.attempts
+        del x, alone
+        if n <= 1 << 20:
+            ref, rinfo = (oracle.sort if op else oracle.orp)(recs, r.Z, seed, method=oracle.CLOSED)
+            np.testing.assert_array_equal(out, ref)
+            assert r.attempts == rinfo.attempts
+        elif op == 0:
+            B, _ = oracle.geometry(n, r.Z)
+            buckets = np.array([0, 1, B // 3, B - 1], dtype=np.uint64)
+            off, load, src = oracle.orp_sample(n, r.Z, seed, buckets, attempt=r.attempts - 1)
+            for b, o, m, s in zip(buckets, off, load, src):
+                np.testing.assert_array_equal(out[int(o):int(o) + int(m)], recs[s])
+        else:
+            keys = out["key"]
+            assert (keys[1:] >= keys[:-1]).all()
+            np.testing.assert_array_equal(np.sort(out, order=["key", "payload"]),
+                                          np.sort(recs, order=["key", "payload"]))
+        torch.cuda.empty_cache()
