@@ -186,6 +186,48 @@ bos_status bos_batched_collect(const void* d_in, void* d_out, const uint64_t* h_
                                const uint8_t* h_ops, const bos_params* base, void* d_ws,
                                size_t ws_bytes, void* stream, uint32_t* h_attempts);
 
+/* Shard plan: the bucket ORP of one array over G = 2^g ranks (GPUs) with one fixed exchange
+ * (the multi-GPU form of Algorithm 3.1's butterfly; the paper has no multi-GPU section). Rank r
+ * holds buckets [r Bl, (r+1) Bl), Bl = B / G, and the input records of their groups,
+ * [bos_shard_input_range). Steps of one attempt (every rank uses the same attempt counter):
+ *   1. bos_shard_local: levels 0 .. L-g-1, which pair buckets inside aligned blocks of at most Bl
+ *      buckets, on the rank's own buckets; its buckets end in the send region of its workspace.
+ *   2. the exchange (the caller's: one all-to-all of whole buckets, NCCL or peer copies): rank s
+ *      sends rank d the chunk d of its send region (chunk_rec_bytes of records at
+ *      send_rec_offset + d * chunk_rec_bytes, chunk_tag_bytes of tags at send_tag_offset +
+ *      d * chunk_tag_bytes) into chunk s of rank d's receive region (recv_*_offset + s * chunk).
+ *      Its volume and addresses do not depend on the data, so the plan stays oblivious.
+ *   3. bos_shard_final: the last g levels on the received buckets in one fused pass, the in-bin
+ *      permutation of Section 3.2 (keys of the global bucket indexes) and the strip; the rank's
+ *      reals (its final buckets [r Bl, (r+1) Bl) in order) go to d_out, *h_count of them, and
+ *      *h_overflow tells whether any MergeSplit of the attempt on this rank overflowed.
+ * If any rank overflowed (a max-reduction), every rank repeats with attempt + 1; otherwise rank
+ * r's part belongs at the sum of the counts of ranks < r. The parts, put together, equal bos_orp of
+ * the whole array with the same seed, and the attempts agree. Requirements: G a power of two with
+ * G^2 <= B and L - g >= 2; flags other than the Section 4.1 form and the merge sort as for
+ * bos_orp (BOS_ERR_INVALID otherwise). Workspace per rank: ws_bytes, 256-byte aligned; d_out
+ * holds out_capacity records. Both steps are stream-ordered; bos_shard_final synchronises
+ * `stream` to read the flag and the count. */
+typedef struct {
+  uint64_t B, B_local;   /* buckets in all, buckets per rank */
+  uint32_t L, g;         /* log2 B, log2 G */
+  uint32_t local_passes; /* HBM passes of step 1 */
+  size_t ws_bytes;       /* workspace bytes per rank */
+  size_t send_rec_offset, send_tag_offset, recv_rec_offset, recv_tag_offset;  /* in the workspace */
+  size_t chunk_rec_bytes, chunk_tag_bytes;  /* one rank-to-rank chunk of the exchange */
+  uint64_t out_capacity; /* records d_out must hold for bos_shard_final */
+} bos_shard_layout_t;
+bos_status bos_shard_layout(uint64_t n, uint32_t G, const bos_params* p, bos_shard_layout_t* out);
+/* Input records [*lo, *hi) of rank r: the groups of its buckets (Algorithm 3.1's placement). */
+bos_status bos_shard_input_range(uint64_t n, uint32_t G, uint32_t r, const bos_params* p, uint64_t* lo,
+                                 uint64_t* hi);
+/* d_in: rank r's input records (its range only, aligned to rec_bytes). */
+bos_status bos_shard_local(const void* d_in, uint64_t n, uint32_t G, uint32_t r, const bos_params* p,
+                           uint32_t attempt, void* d_ws, size_t ws_bytes, void* stream);
+bos_status bos_shard_final(uint64_t n, uint32_t G, uint32_t r, const bos_params* p, uint32_t attempt,
+                           void* d_out, uint64_t out_cap, void* d_ws, size_t ws_bytes, void* stream,
+                           uint64_t* h_count, uint32_t* h_overflow);
+
 /* GPU bitonic sorting network (Table 1's comparator; not oblivious-sort output compatible:
  * equal keys are ordered by payload). n must be a power of two (BOS_ERR_INVALID otherwise).
  * Sorts d_in into d_out by (key, payload) ascending. Needs no workspace. */

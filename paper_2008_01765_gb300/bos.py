@@ -44,6 +44,15 @@ class Info(ctypes.Structure):
                 ("stream_passes", ctypes.c_uint32)]
 
 
+class ShardLayout(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_uint64), ("B_local", ctypes.c_uint64), ("L", ctypes.c_uint32),
+                ("g", ctypes.c_uint32), ("local_passes", ctypes.c_uint32), ("ws_bytes", ctypes.c_size_t),
+                ("send_rec_offset", ctypes.c_size_t), ("send_tag_offset", ctypes.c_size_t),
+                ("recv_rec_offset", ctypes.c_size_t), ("recv_tag_offset", ctypes.c_size_t),
+                ("chunk_rec_bytes", ctypes.c_size_t), ("chunk_tag_bytes", ctypes.c_size_t),
+                ("out_capacity", ctypes.c_uint64)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint32),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -91,6 +100,16 @@ def lib():
         L.bos_bitonic_sort.restype = ctypes.c_int
         L.bos_trace_attach.argtypes = [_vp, ctypes.c_size_t]
         L.bos_trace_attach.restype = ctypes.c_int
+        L.bos_shard_layout.argtypes = [_u64, _u32, ctypes.POINTER(Params), ctypes.POINTER(ShardLayout)]
+        L.bos_shard_layout.restype = ctypes.c_int
+        L.bos_shard_input_range.argtypes = [_u64, _u32, _u32, ctypes.POINTER(Params), ctypes.POINTER(_u64),
+                                            ctypes.POINTER(_u64)]
+        L.bos_shard_input_range.restype = ctypes.c_int
+        L.bos_shard_local.argtypes = [_vp, _u64, _u32, _u32, ctypes.POINTER(Params), _u32, _vp, ctypes.c_size_t, _vp]
+        L.bos_shard_local.restype = ctypes.c_int
+        L.bos_shard_final.argtypes = [_u64, _u32, _u32, ctypes.POINTER(Params), _u32, _vp, _u64, _vp,
+                                      ctypes.c_size_t, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]
+        L.bos_shard_final.restype = ctypes.c_int
         L.bos_trace_attach_digest.argtypes = [_vp, ctypes.c_size_t]
         L.bos_trace_attach_digest.restype = ctypes.c_int
         L.bos_status_str.argtypes = [ctypes.c_int]
@@ -294,6 +313,66 @@ def trace_attach(buf):
     else:
         _check(lib().bos_trace_attach(_vp(buf.data_ptr()), buf.numel() * buf.element_size()),
                "bos_trace_attach")
+
+
+def shard_layout(n, G, p: Params) -> ShardLayout:
+    """bos_shard_layout: geometry and workspace layout of the G-rank shard plan."""
+    lay = ShardLayout()
+    _check(lib().bos_shard_layout(n, G, ctypes.byref(p), ctypes.byref(lay)), "bos_shard_layout")
+    return lay
+
+
+def shard_input_range(n, G, r, p: Params):
+    lo, hi = _u64(), _u64()
+    _check(lib().bos_shard_input_range(n, G, r, ctypes.byref(p), ctypes.byref(lo), ctypes.byref(hi)),
+           "bos_shard_input_range")
+    return lo.value, hi.value
+
+
+def sharded_orp(x, rec_bytes, G, Z=512, seed=1, k=0, max_attempts=8, flags=0, stream=None):
+    """The G-rank shard plan run on one device (each rank its own workspace; the exchange is a
+    device copy of every rank-to-rank chunk). Returns (out, attempts, counts per rank)."""
+    import torch
+    n = x.numel() * x.element_size() // rec_bytes
+    p = params(rec_bytes, Z, seed, k, 0, flags)
+    lay = shard_layout(n, G, p)
+    sh = _stream_handle(stream)
+    ws = [alloc_workspace(lay.ws_bytes, x.device) for _ in range(G)]
+    parts = [torch.empty(lay.out_capacity * rec_bytes, dtype=torch.uint8, device=x.device) for _ in range(G)]
+    ranges = [shard_input_range(n, G, r, p) for r in range(G)]
+    for attempt in range(max_attempts):
+        for r in range(G):
+            lo, hi = ranges[r]
+            _check(lib().bos_shard_local(_vp(x.data_ptr() + lo * rec_bytes), n, G, r, ctypes.byref(p), attempt,
+                                         _vp(ws[r].data_ptr()), ws[r].numel(), sh), "bos_shard_local")
+        with torch.cuda.stream(stream) if stream is not None else _nullctx():
+            for s in range(G):
+                for d in range(G):
+                    for src_off, dst_off, cb in ((lay.send_rec_offset, lay.recv_rec_offset, lay.chunk_rec_bytes),
+                                                 (lay.send_tag_offset, lay.recv_tag_offset, lay.chunk_tag_bytes)):
+                        ws[d][dst_off + s * cb:dst_off + (s + 1) * cb].copy_(
+                            ws[s][src_off + d * cb:src_off + (d + 1) * cb])
+        counts, over = [], False
+        for r in range(G):
+            c, o = _u64(), _u32()
+            _check(lib().bos_shard_final(n, G, r, ctypes.byref(p), attempt, _vp(parts[r].data_ptr()),
+                                         lay.out_capacity, _vp(ws[r].data_ptr()), ws[r].numel(), sh,
+                                         ctypes.byref(c), ctypes.byref(o)), "bos_shard_final")
+            counts.append(int(c.value))
+            over |= bool(o.value)
+        if over:
+            continue
+        out = torch.cat([parts[r][:counts[r] * rec_bytes] for r in range(G)])
+        return out, attempt + 1, counts
+    raise BosError(ERR_OVERFLOW, "sharded_orp")
+
+
+class _nullctx:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
 
 
 def trace_attach_digest(buf):

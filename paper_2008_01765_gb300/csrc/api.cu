@@ -958,6 +958,68 @@ bos_status batch_collect(const BatchIn& b, const BatchLayout& L, char* ws, cudaS
 
 }  // namespace
 
+// ============================================================================================
+// Shard plan: Algorithm 3.1 over G = 2^g ranks with one fixed exchange (the multi-GPU form of the
+// butterfly). Rank r holds buckets [r Bl, (r+1) Bl), Bl = B / G: levels 0 .. L-g-1 pair buckets
+// inside aligned blocks of at most Bl and run locally (the rank's passes over its buckets, with
+// global label bits and group ranges); then rank s sends rank d its local buckets
+// [d Bl/G, (d+1) Bl/G) (whole buckets: volume and addresses do not depend on the data); rank d's
+// received buckets, s-major, are the inputs of the subproblems t in [d Bl/G, (d+1) Bl/G) of the
+// last g levels, which one fused LAST pass runs (local level count L - g, so the routing digit is
+// the label's low g bits), leaving rank d its final buckets [d Bl, (d+1) Bl), permuted by the
+// Section 3.2 keys of their global indexes and stripped of dummies.
+// ============================================================================================
+namespace {
+
+struct ShardPlan {
+  Plan lp;            // the local levels as a plan over Bl buckets (its workspace layout)
+  uint64_t B = 0, Bl = 0;
+  uint32_t L = 0, g = 0, G = 0, kC = 1;  // kC: cluster size of the final pass (Z multiple of 32)
+  bool fast_final = false;
+  size_t send_rec = 0, send_tag = 0, recv_rec = 0, recv_tag = 0, chunk_rec = 0, chunk_tag = 0;
+};
+
+bos_status shard_plan(uint64_t n, uint32_t G, const bos_params* p, ShardPlan* sp) {
+  if (!p || G < 2 || (G & (G - 1)) || (p->flags & (BOS_FLAG_OBLIVIOUS_SPLIT | BOS_FLAG_MERGE_SORT))) return BOS_ERR_INVALID;
+  Plan full;
+  bos_status s = make_plan(n, p, false, &full);
+  if (s != BOS_OK) return s;
+  uint32_t g = 0;
+  while ((1u << g) < G) ++g;
+  if ((uint64_t)G * G > full.B) return BOS_ERR_INVALID;  // every rank sends every rank a whole bucket
+  sp->B = full.B;
+  sp->L = full.L;
+  sp->g = g;
+  sp->G = G;
+  sp->Bl = full.B / G;
+  // the local levels: a plan over Bl buckets of L - g levels (n' fills them exactly)
+  bos_params q = *p;
+  q.flags &= ~(uint32_t)BOS_FLAG_PLAN_ONLY;
+  s = make_plan(sp->Bl * p->Z / 2, &q, false, &sp->lp);
+  if (s != BOS_OK) return s;
+  if (sp->lp.B != sp->Bl || sp->lp.L != full.L - g) return BOS_ERR_INVALID;
+  // the final pass: g levels in one LAST pass
+  sp->fast_final = sp->lp.fast;
+  if (sp->fast_final) {
+    uint32_t C = 1;
+    while (C <= 16 && (g > max_k_fast(sp->lp.R, p->Z, C, true) || (1u << g) < C)) C <<= 1;
+    if (C > 16) sp->fast_final = false; else sp->kC = C;
+  }
+  if (!sp->fast_final && g > max_k(sp->lp.R, p->Z, true)) return BOS_ERR_INVALID;
+  // the local step leaves its buckets in slot array (passes - 1) & 1; the exchange fills the other
+  const uint32_t last = (sp->lp.npass - 1) & 1, other = last ^ 1;
+  if (sp->lp.L < 2) return BOS_ERR_INVALID;  // both slot arrays exist only when L - g >= 2
+  sp->send_rec = sp->lp.off_rec[last];
+  sp->send_tag = sp->lp.off_tag[last];
+  sp->recv_rec = sp->lp.off_rec[other];
+  sp->recv_tag = sp->lp.off_tag[other];
+  sp->chunk_rec = (size_t)(sp->Bl / G) * p->Z * sp->lp.R;
+  sp->chunk_tag = (size_t)(sp->Bl / G) * p->Z * 4;
+  return BOS_OK;
+}
+
+}  // namespace
+
 size_t orp_workspace_bytes(uint64_t n, const bos_params* p) {
   Plan pl;
   if (make_plan(n, p, false, &pl) != BOS_OK) return 0;
@@ -1053,6 +1115,160 @@ bos_status bos_sort_batched(const void* d_in, void* d_out, const uint64_t* h_off
   if (s != BOS_OK) return s;
   return bos_batched_collect(d_in, d_out, h_offsets, num, h_seeds, h_Z, h_ops, base, d_ws, ws_bytes, stream,
                              h_attempts);
+}
+
+bos_status bos_shard_layout(uint64_t n, uint32_t G, const bos_params* p, bos_shard_layout_t* out) {
+  ShardPlan sp;
+  const bos_status s = shard_plan(n, G, p, &sp);
+  if (s != BOS_OK || !out) return s != BOS_OK ? s : BOS_ERR_INVALID;
+  out->B = sp.B;
+  out->B_local = sp.Bl;
+  out->L = sp.L;
+  out->g = sp.g;
+  out->local_passes = sp.lp.npass;
+  out->ws_bytes = sp.lp.total;
+  out->send_rec_offset = sp.send_rec;
+  out->send_tag_offset = sp.send_tag;
+  out->recv_rec_offset = sp.recv_rec;
+  out->recv_tag_offset = sp.recv_tag;
+  out->chunk_rec_bytes = sp.chunk_rec;
+  out->chunk_tag_bytes = sp.chunk_tag;
+  out->out_capacity = sp.Bl * p->Z;
+  return BOS_OK;
+}
+
+bos_status bos_shard_input_range(uint64_t n, uint32_t G, uint32_t r, const bos_params* p, uint64_t* lo,
+                                 uint64_t* hi) {
+  ShardPlan sp;
+  const bos_status s = shard_plan(n, G, p, &sp);
+  if (s != BOS_OK) return s;
+  if (r >= G || !lo || !hi) return BOS_ERR_INVALID;
+  *lo = ((uint64_t)r * sp.Bl * n) >> sp.L;
+  *hi = ((uint64_t)(r + 1) * sp.Bl * n) >> sp.L;
+  return BOS_OK;
+}
+
+bos_status bos_shard_local(const void* d_in, uint64_t n, uint32_t G, uint32_t r, const bos_params* p,
+                           uint32_t attempt, void* d_ws, size_t ws_bytes, void* stream) {
+  ShardPlan sp;
+  bos_status s = shard_plan(n, G, p, &sp);
+  if (s != BOS_OK) return s;
+  if (r >= G || !d_ws || ((uintptr_t)d_ws & 255) || (!d_in && n)) return BOS_ERR_INVALID;
+  if (ws_bytes < sp.lp.total) return BOS_ERR_WORKSPACE;
+  const Plan& pl = sp.lp;
+  if ((uintptr_t)d_in % pl.R) return BOS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  Ctrl* ctrl = (Ctrl*)(ws + pl.off_ctrl);
+  const uint64_t lo = ((uint64_t)r * sp.Bl * n) >> sp.L;
+  const Trace tr = trace_snapshot();
+  BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  for (uint32_t x = 0; x < pl.npass; ++x) {
+    PassArgs a{};
+    const bool first = x == 0;
+    const uint32_t src = (x + 1) & 1, dst = x & 1;
+    // the rank's input slice starts at global record lo: the kernels index records globally
+    a.in = (const char*)d_in - lo * pl.R;
+    if (!first) {
+      a.in_rec = ws + pl.off_rec[src];
+      a.in_tag = (const uint32_t*)(ws + pl.off_tag[src]);
+      a.buf_in_rec = src ? kBufRecB : kBufRecA;
+      a.buf_in_tag = src ? kBufTagB : kBufTagA;
+    }
+    a.out_rec = ws + pl.off_rec[dst];
+    a.out_tag = (uint32_t*)(ws + pl.off_tag[dst]);
+    a.buf_out_rec = dst ? kBufRecB : kBufRecA;
+    a.buf_out_tag = dst ? kBufTagB : kBufTagA;
+    a.n = n;
+    a.B = sp.Bl;
+    a.Z = pl.Z;
+    a.L = sp.L;  // global label width: levels 0 .. L-g-1 route on its top bits
+    a.i = pl.pass_i[x];
+    a.k = pl.pass_k[x];
+    a.attempt = attempt;
+    a.seed = p->seed;
+    a.ctrl = ctrl;
+    a.trace = tr;
+    a.bucket0 = (uint64_t)r * sp.Bl;
+    const int mode = first ? kModeFirst : 0;
+    if (pl.pass_stream[x])
+      BOS_CUDA(launch_orp_stream(a, first, st, pl.R, tr.buf != nullptr));
+    else if (pl.fast)
+      BOS_CUDA(launch_orp_fast(a, mode, pl.pass_C[x], 0, st, pl.R, tr.buf != nullptr));
+    else
+      BOS_CUDA(launch_orp_pass(a, mode, sp.Bl >> a.k, st, pl.R, tr.buf != nullptr));
+  }
+  return BOS_OK;
+}
+
+bos_status bos_shard_final(uint64_t n, uint32_t G, uint32_t r, const bos_params* p, uint32_t attempt,
+                           void* d_out, uint64_t out_cap, void* d_ws, size_t ws_bytes, void* stream,
+                           uint64_t* h_count, uint32_t* h_overflow) {
+  ShardPlan sp;
+  bos_status s = shard_plan(n, G, p, &sp);
+  if (s != BOS_OK) return s;
+  if (r >= G || !d_ws || ((uintptr_t)d_ws & 255) || !d_out || !h_count || !h_overflow) return BOS_ERR_INVALID;
+  if (ws_bytes < sp.lp.total) return BOS_ERR_WORKSPACE;
+  const Plan& pl = sp.lp;
+  if ((uintptr_t)d_out % pl.R || overlaps(d_out, out_cap * pl.R, d_ws, ws_bytes)) return BOS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  Ctrl* ctrl = (Ctrl*)(ws + pl.off_ctrl);
+  const Trace tr = trace_snapshot();
+  const uint64_t nsub = sp.Bl >> sp.g;
+  // the local step's overflow flag stays; the tickets and look-back words start at zero
+  BOS_CUDA(cudaMemsetAsync(&ctrl->tickets[0], 0, sizeof(ctrl->tickets), st));
+  BOS_CUDA(cudaMemsetAsync(ws + pl.off_status, 0, nsub * 8, st));
+  PassArgs a{};
+  a.in_rec = ws + sp.recv_rec;
+  a.in_tag = (const uint32_t*)(ws + sp.recv_tag);
+  a.buf_in_rec = sp.recv_rec == pl.off_rec[1] ? kBufRecB : kBufRecA;
+  a.buf_in_tag = sp.recv_rec == pl.off_rec[1] ? kBufTagB : kBufTagA;
+  a.out0 = a.out1 = d_out;
+  a.out_sel = 0;
+  a.status = (unsigned long long*)(ws + pl.off_status);
+  a.ord = (const uint16_t*)(ws + pl.off_ord);
+  a.n = out_cap;  // bound of the output positions
+  a.B = sp.Bl;
+  a.Z = pl.Z;
+  a.L = sp.L - sp.g;  // local level count: the routing digit is the label's low g bits
+  a.i = sp.L - 2 * sp.g;
+  a.k = sp.g;
+  a.attempt = attempt;
+  a.seed = p->seed;
+  a.ctrl = ctrl;
+  a.trace = tr;
+  a.bucket0 = (uint64_t)r * sp.Bl;
+  if (sp.fast_final) {
+    PermTableArgs ta{};
+    ta.bucket0 = a.bucket0;
+    ta.ord = (uint16_t*)(ws + pl.off_ord);
+    ta.tag = a.in_tag;
+    ta.load = (uint32_t*)(ws + pl.off_load);
+    ta.B = sp.Bl;
+    ta.Z = pl.Z;
+    ta.attempt = attempt;
+    ta.i = a.i;
+    ta.k = a.k;
+    ta.L = a.L;
+    ta.buf_tag = a.buf_in_tag;
+    ta.seed = p->seed;
+    ta.trace = tr;
+    BOS_CUDA(launch_perm_table(ta, st, tr.buf != nullptr));
+    BOS_CUDA(launch_orp_fast(a, kModeLast, sp.kC, 0, st, pl.R, tr.buf != nullptr));
+  } else {
+    BOS_CUDA(launch_orp_pass(a, kModeLast, nsub, st, pl.R, tr.buf != nullptr));
+  }
+  Ctrl h{};
+  unsigned long long last = 0;
+  BOS_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  BOS_CUDA(cudaMemcpyAsync(&last, ws + pl.off_status + (nsub - 1) * 8, 8, cudaMemcpyDeviceToHost, st));
+  BOS_CUDA(cudaStreamSynchronize(st));
+  if (h.timeout) return BOS_ERR_TIMEOUT;
+  *h_overflow = h.overflow ? 1u : 0u;
+  *h_count = last & kStValue;  // the last subproblem's inclusive prefix: the rank's reals
+  if (!h.overflow && *h_count > out_cap) return BOS_ERR_INVALID;
+  return BOS_OK;
 }
 
 bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t rec_bytes,

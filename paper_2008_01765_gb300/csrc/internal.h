@@ -30,6 +30,8 @@ struct PassArgs {
   uint32_t buf_in_rec, buf_in_tag, buf_out_rec, buf_out_tag;  // trace buffer ids
   Trace trace;
   const uint16_t* ord;      // LAST (persistent kernel): in-bin permutation table, B*Z slot indexes
+  uint64_t bucket0;         // global index of local bucket 0 (a shard's buckets; 0 otherwise): the
+                            // first pass's groups and the in-bin permutation keys use global indexes
 };
 
 // In-bin permutation table (perm_table.cu): row b < B lists final bucket b's slots in the order
@@ -38,6 +40,7 @@ struct PassArgs {
 // 0xFFFF, m counted first into load[b] by a kernel of its own; without them, all Z slots. Z a
 // multiple of 32, <= 4096; k <= 12.
 struct PermTableArgs {
+  uint64_t bucket0;      // global index of local bucket 0 (the keys use global bucket indexes)
   uint16_t* ord;
   const uint32_t* tag;
   uint32_t* load;        // [B] reals per final bucket (workspace), written and read here

@@ -120,8 +120,8 @@ __device__ __forceinline__ void orp_pass_body(const PassArgs& a, uint64_t q) {
       if (p < S) {
         const uint32_t s = p / Z, sl = p - s * Z;
         if constexpr (FIRST) {
-          const uint64_t j = q * D + s;  // group index (i = 0)
-          const uint64_t lo = (j * a.n) / a.B, hi = ((j + 1) * a.n) / a.B;
+          const uint64_t j = a.bucket0 + q * D + s;  // group index (i = 0); B = 2^L
+          const uint64_t lo = (j * a.n) >> a.L, hi = ((j + 1) * a.n) >> a.L;
           if (lo + sl < hi) {
             const uint64_t idx = lo + sl;
             load_rec<R>(rc[it], a.in, idx);
@@ -224,7 +224,7 @@ __device__ __forceinline__ void orp_pass_body(const PassArgs& a, uint64_t q) {
       uint16_t* members = reinterpret_cast<uint16_t*>(bin_cur + 256);
       for (uint32_t u = warp; u < D; u += kPermWarps) {
         const uint32_t m = min(base[u], Z);
-        const uint64_t b = q * D + u;
+        const uint64_t b = a.bucket0 + q * D + u;  // global bucket: the key's counter
         uint32_t* rhi = tile_tag + u * Z;  // tags are dead in the last pass: reuse as key store
         for (int x = lane; x < 256; x += 32) bin_cur[x] = 0;
         __syncwarp();

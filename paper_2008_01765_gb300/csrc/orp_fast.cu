@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
   // in the input array (FIRST: its group's first record; lim = the group's size).
   auto bucket_base = [&](uint64_t qq, uint32_t sp, uint64_t& base, uint32_t& lim) {
     if constexpr (FIRST) {
-      const uint64_t g = qq * D + crank * Dc + sp;
+      const uint64_t g = a.bucket0 + qq * D + crank * Dc + sp;
       const uint64_t lo = (g * a.n) >> L, hi = ((g + 1) * a.n) >> L;  // group g, B = 2^L
       base = lo;
       lim = (uint32_t)(hi - lo);

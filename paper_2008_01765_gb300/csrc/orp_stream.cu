@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
 
   // first pass: batch s of subproblem q = groups q*D + 2s and q*D + 2s + 1 (B = 2^L)
   auto first_range = [&](uint64_t q, uint32_t s, uint64_t& lo, uint64_t& hi) {
-    const uint64_t g0 = q * D + 2ull * s;
+    const uint64_t g0 = a.bucket0 + q * D + 2ull * s;
     lo = (g0 * a.n) >> L;
     hi = ((g0 + 2) * a.n) >> L;
   };

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256, 3) perm_table_kernel(PermTableArgs a) {
   const bool tagged = a.tag != nullptr;
 
   for (uint64_t b = (uint64_t)blockIdx.x * W + warp; b < a.B; b += (uint64_t)gridDim.x * W) {
-    const uint64_t base = b * Z;
+    const uint64_t base = (a.bucket0 + b) * Z;  // the keys' counters use the global bucket
     const uint32_t m = tagged ? min(a.load[b], Z) : Z;
     for (int x = lane; x < kPBins; x += 32) bins[x] = 0;
     __syncwarp();
@@ -182,10 +182,10 @@ __global__ void __launch_bounds__(256, 3) perm_table_kernel(PermTableArgs a) {
     for (uint32_t s = m + lane; s < Z; s += 32) row[s] = 0xFFFFu;  // no real at these ranks
     __syncwarp();
     // Z is a multiple of 32: the bucket's row is whole 16-byte words, 16-byte aligned
-    uint4* dst = reinterpret_cast<uint4*>(a.ord + base);
+    uint4* dst = reinterpret_cast<uint4*>(a.ord + b * Z);
     const uint4* src = reinterpret_cast<const uint4*>(row);
     for (uint32_t x = lane; x < Z / 8; x += 32) dst[x] = src[x];
-    if (lane == 0) trace_log<TRACE>(a.trace, kWrite, kBufPerm, Z * 2, base * 2);
+    if (lane == 0) trace_log<TRACE>(a.trace, kWrite, kBufPerm, Z * 2, b * Z * 2);
     __syncwarp();  // the warp's next bucket reuses its arrays
   }
 }

@@ -122,3 +122,30 @@ def test_plans_cover_every_level(bos):
                 assert plans["nocl"].passes <= plans["nocl_nostream"].passes, (R, Z, n)
                 assert plans["nostream"].stream_passes == 0
                 assert "generic" not in plans or plans["generic"].stream_passes == 0
+
+
+def test_shard_layout_and_input_ranges(bos):
+    # The shard plan's geometry (no device work): B_local = B / G, g = log2 G, the local step runs
+    # L - g levels, the send and receive regions lie inside the workspace and hold G chunks of
+    # B_local / G whole buckets each, and the ranks' input ranges tile [0, n) in rank order.
+    import oracle
+    for R, Z, n, G in [(8, 64, 5000, 2), (16, 512, 1 << 20, 4), (16, 1024, (1 << 22) + 5, 8), (8, 96, 300001, 4)]:
+        p = bos.params(R, Z, 1)
+        lay = bos.shard_layout(n, G, p)
+        B, L = oracle.geometry(n, Z)
+        assert (lay.B, lay.L, lay.B_local, 1 << lay.g) == (B, L, B // G, G)
+        assert lay.chunk_rec_bytes == (B // G // G) * Z * R and lay.chunk_tag_bytes == (B // G // G) * Z * 4
+        for off, cb in ((lay.send_rec_offset, lay.chunk_rec_bytes), (lay.recv_rec_offset, lay.chunk_rec_bytes),
+                        (lay.send_tag_offset, lay.chunk_tag_bytes), (lay.recv_tag_offset, lay.chunk_tag_bytes)):
+            assert off % 256 == 0 and off + G * cb <= lay.ws_bytes
+        assert lay.send_rec_offset != lay.recv_rec_offset
+        end = 0
+        for r in range(G):
+            lo, hi = bos.shard_input_range(n, G, r, p)
+            assert lo == end and hi >= lo
+            end = hi
+        assert end == n
+    with pytest.raises(bos.BosError):
+        bos.shard_layout(5000, 3, bos.params(8, 64, 1))  # not a power of two
+    with pytest.raises(bos.BosError):
+        bos.shard_layout(100, 8, bos.params(8, 64, 1))  # G^2 > B

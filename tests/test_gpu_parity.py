@@ -569,3 +569,32 @@ def test_batched_kernel_trace_is_input_independent(bos):
         np.testing.assert_array_equal(_batch_trace(bos, sizes, 8, dist, seeds, Zs, ops), base)
     t2 = _batch_trace(bos, sizes, 8, "uniform", seeds + np.uint64(1000), Zs, ops)
     np.testing.assert_array_equal(t2[_kind_buf(t2) != 5], base[_kind_buf(base) != 5])
+
+
+SHARD_CASES = [
+    # (G, n, Z, rec_bytes, k): the shard plan on one device, against bos_orp and the oracle
+    (2, 1 << 16, 512, 8, 0), (4, (1 << 20) + 3, 512, 16, 0), (2, 300001, 96, 16, 0), (8, 1 << 22, 1024, 16, 0),
+    (4, 100003, 64, 8, 1), (2, 50000, 40, 8, 0), (4, 20000, 32, 8, 0),  # the last two overflow and retry
+]
+
+
+@pytest.mark.parametrize("G,n,Z,rec_bytes,k", SHARD_CASES)
+def test_shard_plan_on_gpu_equals_single_device(bos, G, n, Z, rec_bytes, k):
+    # Local levels on every rank's buckets, one all-to-all of whole buckets (device copies here),
+    # the fused last levels with the in-bin permutation: the ranks' parts in rank order equal
+    # bos_orp of the whole array and the oracle, with the same attempts (Algorithm 3.1).
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=n % 997 + G)
+    seed = 77 + G
+    x = bos.to_device(recs)
+    try:
+        ref, rinfo = oracle.orp(recs, Z, seed, max_attempts=16, method=oracle.CLOSED)
+    except oracle.OracleError:
+        with pytest.raises(bos.BosError):
+            bos.sharded_orp(x, rec_bytes, G, Z=Z, seed=seed, k=k, max_attempts=16)
+        return
+    out, attempts, counts = bos.sharded_orp(x, rec_bytes, G, Z=Z, seed=seed, k=k, max_attempts=16)
+    got = bos.to_host(out, recs.dtype)
+    assert attempts == rinfo.attempts and sum(counts) == n
+    np.testing.assert_array_equal(got, ref)
+    alone, ainfo = gpu_orp(bos, recs, Z, seed, k=k, max_attempts=16)
+    np.testing.assert_array_equal(got, alone)
