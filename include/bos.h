@@ -228,6 +228,23 @@ bos_status bos_shard_final(uint64_t n, uint32_t G, uint32_t r, const bos_params*
                            void* d_out, uint64_t out_cap, void* d_ws, size_t ws_bytes, void* stream,
                            uint64_t* h_count, uint32_t* h_overflow);
 
+/* Out-of-core bucket ORP: n records in host memory, more than the device can hold (Section 4.3's
+ * setting, where the data live in a slower, larger memory and are accessed in large contiguous
+ * runs). The shard plan above runs its G ranks one after another on the current GPU, each rank's
+ * data staying in host memory between its steps: rank r's input range goes in, its local levels
+ * run, its send regions go to h_stage; then, for every rank d, its chunks are gathered from
+ * h_stage, its last levels, in-bin permutation and strip run, and its part goes to h_out at the
+ * sum of the earlier parts. Every host access is a contiguous run of whole buckets (their volume
+ * and addresses do not depend on the data). Same result as bos_orp for the same arguments.
+ * h_in, h_out: n records of host memory (pinned for full copy bandwidth); d_buf: dev_bytes of
+ * device memory (256-byte aligned); h_stage: host_bytes of host memory; both from
+ * bos_orp_out_of_core_bytes. G as for the shard plan. Synchronises `stream`. */
+bos_status bos_orp_out_of_core_bytes(uint64_t n, uint32_t G, const bos_params* p, size_t* dev_bytes,
+                                     size_t* host_bytes);
+bos_status bos_orp_out_of_core(const void* h_in, void* h_out, uint64_t n, const bos_params* p, uint32_t G,
+                               void* d_buf, size_t dev_bytes, void* h_stage, size_t host_bytes, void* stream,
+                               bos_info* info);
+
 /* GPU bitonic sorting network (Table 1's comparator; not oblivious-sort output compatible:
  * equal keys are ordered by payload). n must be a power of two (BOS_ERR_INVALID otherwise).
  * Sorts d_in into d_out by (key, payload) ascending. Needs no workspace. */

@@ -110,6 +110,12 @@ def lib():
         L.bos_shard_final.argtypes = [_u64, _u32, _u32, ctypes.POINTER(Params), _u32, _vp, _u64, _vp,
                                       ctypes.c_size_t, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]
         L.bos_shard_final.restype = ctypes.c_int
+        L.bos_orp_out_of_core_bytes.argtypes = [_u64, _u32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t),
+                                                ctypes.POINTER(ctypes.c_size_t)]
+        L.bos_orp_out_of_core_bytes.restype = ctypes.c_int
+        L.bos_orp_out_of_core.argtypes = [_vp, _vp, _u64, ctypes.POINTER(Params), _u32, _vp, ctypes.c_size_t, _vp,
+                                          ctypes.c_size_t, _vp, ctypes.POINTER(Info)]
+        L.bos_orp_out_of_core.restype = ctypes.c_int
         L.bos_trace_attach_digest.argtypes = [_vp, ctypes.c_size_t]
         L.bos_trace_attach_digest.restype = ctypes.c_int
         L.bos_status_str.argtypes = [ctypes.c_int]
@@ -365,6 +371,28 @@ def sharded_orp(x, rec_bytes, G, Z=512, seed=1, k=0, max_attempts=8, flags=0, st
         out = torch.cat([parts[r][:counts[r] * rec_bytes] for r in range(G)])
         return out, attempt + 1, counts
     raise BosError(ERR_OVERFLOW, "sharded_orp")
+
+
+def orp_out_of_core(recs: np.ndarray, G, Z=512, seed=1, k=0, max_attempts=0, flags=0, device="cuda",
+                    stream=None):
+    """bos_orp_out_of_core of a host record array (copied to pinned host memory); returns
+    (host result array, Info). The device holds one rank's share of the shard plan at a time."""
+    import torch
+    rec_bytes = recs.dtype.itemsize
+    n = recs.shape[0]
+    p = params(rec_bytes, Z, seed, k, max_attempts, flags)
+    dev_b, host_b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().bos_orp_out_of_core_bytes(n, G, ctypes.byref(p), ctypes.byref(dev_b), ctypes.byref(host_b)),
+           "bos_orp_out_of_core_bytes")
+    h_in = torch.from_numpy(np.ascontiguousarray(recs).view(np.uint8).reshape(-1)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    h_stage = torch.empty(max(host_b.value, 1), dtype=torch.uint8).pin_memory()
+    d_buf = alloc_workspace(dev_b.value, device)
+    info = Info()
+    _check(lib().bos_orp_out_of_core(_vp(h_in.data_ptr()), _vp(h_out.data_ptr()), n, ctypes.byref(p), G,
+                                     _vp(d_buf.data_ptr()), d_buf.numel(), _vp(h_stage.data_ptr()), h_stage.numel(),
+                                     _stream_handle(stream), ctypes.byref(info)), "bos_orp_out_of_core")
+    return h_out.numpy().view(recs.dtype).copy(), info
 
 
 class _nullctx:

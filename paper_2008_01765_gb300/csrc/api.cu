@@ -1271,6 +1271,106 @@ bos_status bos_shard_final(uint64_t n, uint32_t G, uint32_t r, const bos_params*
   return BOS_OK;
 }
 
+bos_status bos_orp_out_of_core_bytes(uint64_t n, uint32_t G, const bos_params* p, size_t* dev_bytes,
+                                     size_t* host_bytes) {
+  ShardPlan sp;
+  const bos_status s = shard_plan(n, G, p, &sp);
+  if (s != BOS_OK) return s;
+  if (!dev_bytes || !host_bytes) return BOS_ERR_INVALID;
+  const uint64_t slice = (((sp.Bl * n) >> sp.L) + 2);  // input records of one rank, at most
+  *dev_bytes = align256(sp.lp.total) + align256(slice * sp.lp.R) + align256(sp.Bl * p->Z * (uint64_t)sp.lp.R);
+  *host_bytes = (size_t)G * G * (sp.chunk_rec + sp.chunk_tag);
+  return BOS_OK;
+}
+
+bos_status bos_orp_out_of_core(const void* h_in, void* h_out, uint64_t n, const bos_params* p, uint32_t G,
+                               void* d_buf, size_t dev_bytes, void* h_stage, size_t host_bytes, void* stream,
+                               bos_info* info) {
+  ShardPlan sp;
+  bos_status s = shard_plan(n, G, p, &sp);
+  if (s != BOS_OK) return s;
+  size_t need_dev = 0, need_host = 0;
+  bos_orp_out_of_core_bytes(n, G, p, &need_dev, &need_host);
+  if (!h_in || !h_out || !d_buf || !h_stage || ((uintptr_t)d_buf & 255)) return BOS_ERR_INVALID;
+  if (dev_bytes < need_dev || host_bytes < need_host) return BOS_ERR_WORKSPACE;
+  const uint32_t R = sp.lp.R;
+  const size_t ws_bytes = align256(sp.lp.total);
+  const uint64_t slice = ((sp.Bl * n) >> sp.L) + 2;
+  char* d_ws = (char*)d_buf;
+  char* d_in = d_ws + ws_bytes;
+  char* d_part = d_in + align256(slice * R);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t per_rank = (size_t)G * (sp.chunk_rec + sp.chunk_tag);  // host: rank r's send regions
+  char* hs = (char*)h_stage;
+  const uint32_t max_attempts = p->max_attempts ? p->max_attempts : kDefaultAttempts;
+  if (info) {
+    info->L = sp.L;
+    info->B = sp.B;
+    info->passes = sp.lp.npass + 1;
+    info->radix_passes = 0;
+    info->max_cluster = sp.kC;
+    info->max_k = sp.g;
+    info->stream_passes = 0;
+    for (uint32_t x = 0; x < sp.lp.npass; ++x) {
+      info->max_k = sp.lp.pass_k[x] > info->max_k ? sp.lp.pass_k[x] : info->max_k;
+      info->stream_passes += sp.lp.pass_stream[x] ? 1u : 0u;
+    }
+  }
+  for (uint32_t attempt = 0; attempt < max_attempts; ++attempt) {
+    // every rank's local levels; its send regions (G chunks of records, then of tags) to the host
+    for (uint32_t r = 0; r < G; ++r) {
+      uint64_t lo = 0, hi = 0;
+      bos_shard_input_range(n, G, r, p, &lo, &hi);
+      if (hi > lo) BOS_CUDA(cudaMemcpyAsync(d_in, (const char*)h_in + lo * R, (hi - lo) * R, cudaMemcpyHostToDevice, st));
+      if ((s = bos_shard_local(d_in, n, G, r, p, attempt, d_ws, ws_bytes, stream)) != BOS_OK) return s;
+      BOS_CUDA(cudaMemcpyAsync(hs + r * per_rank, d_ws + sp.send_rec, G * sp.chunk_rec, cudaMemcpyDeviceToHost, st));
+      BOS_CUDA(cudaMemcpyAsync(hs + r * per_rank + G * sp.chunk_rec, d_ws + sp.send_tag, G * sp.chunk_tag,
+                               cudaMemcpyDeviceToHost, st));
+      // the local step's overflow flag is kept on the host: the next rank reuses the workspace
+      Ctrl h{};
+      BOS_CUDA(cudaMemcpyAsync(&h, d_ws + sp.lp.off_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      BOS_CUDA(cudaStreamSynchronize(st));
+      if (h.timeout) return BOS_ERR_TIMEOUT;
+      if (h.overflow) goto next_attempt;  // the attempt fails everywhere
+    }
+    {
+      // every rank's received chunks from the host, its last levels, its part to the host output
+      uint64_t offset = 0;
+      bool over = false;
+      for (uint32_t d = 0; d < G && !over; ++d) {
+        for (uint32_t r = 0; r < G; ++r) {
+          BOS_CUDA(cudaMemcpyAsync(d_ws + sp.recv_rec + r * sp.chunk_rec, hs + r * per_rank + d * sp.chunk_rec,
+                                   sp.chunk_rec, cudaMemcpyHostToDevice, st));
+          BOS_CUDA(cudaMemcpyAsync(d_ws + sp.recv_tag + r * sp.chunk_tag,
+                                   hs + r * per_rank + G * sp.chunk_rec + d * sp.chunk_tag, sp.chunk_tag,
+                                   cudaMemcpyHostToDevice, st));
+        }
+        BOS_CUDA(cudaMemsetAsync(d_ws + sp.lp.off_ctrl, 0, sizeof(Ctrl), st));
+        uint64_t count = 0;
+        uint32_t ovf = 0;
+        if ((s = bos_shard_final(n, G, d, p, attempt, d_part, sp.Bl * p->Z, d_ws, ws_bytes, stream, &count, &ovf)) !=
+            BOS_OK)
+          return s;
+        if (ovf) {
+          over = true;
+          break;
+        }
+        if (offset + count > n) return BOS_ERR_INVALID;
+        if (count) BOS_CUDA(cudaMemcpyAsync((char*)h_out + offset * R, d_part, count * R, cudaMemcpyDeviceToHost, st));
+        offset += count;
+      }
+      BOS_CUDA(cudaStreamSynchronize(st));
+      if (!over) {
+        if (info) info->attempts = attempt + 1;
+        return offset == n ? BOS_OK : BOS_ERR_INVALID;
+      }
+    }
+  next_attempt:;
+  }
+  if (info) info->attempts = max_attempts;
+  return BOS_ERR_OVERFLOW;
+}
+
 bos_status bos_bitonic_sort(const void* d_in, void* d_out, uint64_t n, uint32_t rec_bytes,
                             uint32_t key_bytes, void* stream) {
   if (!((rec_bytes == 8 && key_bytes == 4) || (rec_bytes == 16 && key_bytes == 8))) return BOS_ERR_INVALID;

@@ -598,3 +598,26 @@ def test_shard_plan_on_gpu_equals_single_device(bos, G, n, Z, rec_bytes, k):
     np.testing.assert_array_equal(got, ref)
     alone, ainfo = gpu_orp(bos, recs, Z, seed, k=k, max_attempts=16)
     np.testing.assert_array_equal(got, alone)
+
+
+OOC_CASES = [
+    # (G, n, Z, rec_bytes): the out-of-core ORP (host memory, one rank's share on the device)
+    (4, 1 << 22, 1024, 16), (16, (1 << 22) + 77, 512, 16), (4, 100003, 64, 8), (8, 1 << 20, 96, 8),
+    (2, 8192, 32, 8),  # overflows and retries
+]
+
+
+@pytest.mark.parametrize("G,n,Z,rec_bytes", OOC_CASES)
+def test_out_of_core_orp_equals_in_memory(bos, G, n, Z, rec_bytes):
+    # Section 4.3's setting: the data stay in host memory and move in runs of whole buckets; the
+    # result equals bos_orp in device memory and the oracle, with the same attempts.
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=n % 991 + 3)
+    seed = 2 if n == 8192 else 5 + G
+    if n == 8192:
+        recs = inputs.make_records(n, rec_bytes, "uniform", seed=2)
+    ref, rinfo = oracle.orp(recs, Z, seed, max_attempts=16, method=oracle.CLOSED)
+    got, info = bos.orp_out_of_core(recs, G, Z=Z, seed=seed, max_attempts=16)
+    assert info.attempts == rinfo.attempts
+    np.testing.assert_array_equal(got, ref)
+    alone, _ = gpu_orp(bos, recs, Z, seed, max_attempts=16)
+    np.testing.assert_array_equal(got, alone)
