@@ -82,6 +82,11 @@ typedef enum {
 /* Largest thread-block cluster a pass may use (1, 2, 4, 8 or 16; 0 = the library's choice).
  * Tuning only: the result never depends on it. */
 #define BOS_FLAG_MAX_CLUSTER(c) (((uint32_t)(c) & 0x1Fu) << 16)
+/* bos_sort: the LSD radix sort (one pass per live 8-bit digit) instead of the hybrid radix sort
+ * (partitions on the top one or two digits, then an on-chip sort of every group of records that
+ * share them). Same result. The hybrid sort falls back to the LSD passes by itself whenever a
+ * group would exceed one CTA's on-chip capacity. */
+#define BOS_FLAG_LSD_SORT 0x200000u
 
 typedef struct {
   uint32_t rec_bytes;    /* 8 or 16 */
@@ -99,11 +104,15 @@ typedef struct {
   uint32_t attempts; /* attempts run (1 unless an overflow forced a retry) */
   uint32_t L;        /* log2 B, the number of butterfly levels */
   uint32_t passes;   /* HBM passes of the ORP in the last attempt */
-  uint32_t radix_passes; /* LSD radix passes run by the sort (digits where all keys agree are skipped) */
+  uint32_t radix_passes; /* HBM passes of the sort after the ORP, histogram excluded: one per live
+                            8-bit digit for the LSD sort (digits where all keys agree are skipped),
+                            1 to 3 for the hybrid sort */
   uint64_t B;        /* number of buckets: smallest power of two with B * Z >= 2n */
   uint32_t max_cluster; /* largest thread-block cluster used by a pass (1 = no clusters) */
   uint32_t max_k;    /* most butterfly levels fused into one pass */
   uint32_t stream_passes; /* passes run by the streaming kernel (first and middle passes) */
+  uint32_t sort_mode; /* bos_sort's radix sort: 0 LSD; 1 on-chip only; 2 one partition + on-chip;
+                         3 two partitions + on-chip */
 } bos_info;
 
 /* Bytes of device workspace bos_orp / bos_sort need for n records under *p (0 for n = 0):

@@ -21,6 +21,7 @@ FLAG_PLAN_ONLY = 0x10
 FLAG_MERGE_SORT = 0x20
 FLAG_OBLIVIOUS_SPLIT = 0x40
 FLAG_NO_STREAM = 0x80
+FLAG_LSD_SORT = 0x200000
 
 
 def FLAG_FORCE_OVERFLOW(n):
@@ -41,7 +42,7 @@ class Info(ctypes.Structure):
     _fields_ = [("attempts", ctypes.c_uint32), ("L", ctypes.c_uint32), ("passes", ctypes.c_uint32),
                 ("radix_passes", ctypes.c_uint32), ("B", ctypes.c_uint64),
                 ("max_cluster", ctypes.c_uint32), ("max_k", ctypes.c_uint32),
-                ("stream_passes", ctypes.c_uint32)]
+                ("stream_passes", ctypes.c_uint32), ("sort_mode", ctypes.c_uint32)]
 
 
 class ShardLayout(ctypes.Structure):

@@ -32,10 +32,11 @@ Trace trace_snapshot() {
 
 // ---- opt-in kernel timing (bos_profile_enable / bos_profile_read) ----
 enum KClass { kKFirst, kKMid, kKLast, kKSingle, kKHist, kKPrep, kKRadix, kKRadixSkipped, kKBitonic, kKPerm,
-              kKMergeBlock, kKMerge, kKOblivious, kKCount };
+              kKMergeBlock, kKMerge, kKOblivious, kKMsd, kKLocal, kKCount };
 const char* const kKNames[kKCount] = {"orp_pass_first", "orp_pass_mid", "orp_pass_last", "orp_pass_single",
                                      "radix_hist", "radix_prep", "radix_pass", "radix_pass_skipped",
-                                     "bitonic", "perm_table", "merge_block", "merge_pass", "orp_oblivious"};
+                                     "bitonic", "perm_table", "merge_block", "merge_pass", "orp_oblivious",
+                                     "sort_partition", "sort_local"};
 constexpr int kMaxEv = 1024;
 struct Prof {
   std::atomic<bool> on{false};
@@ -69,7 +70,9 @@ void prof_end(int i, cudaStream_t st) {
   if (i >= 0) cudaEventRecord(g_prof.ev[2 * i + 1], st);
 }
 // Folds the finished event pairs into the per-class totals (the stream has been synchronised).
-void prof_collect(uint32_t radix_live) {
+// A launch that returned at once (a constant digit; the LSD passes when the hybrid sort ran; a
+// hybrid stage its mode does not run) counts as a skipped radix pass.
+void prof_collect(uint32_t radix_live, uint32_t sort_mode) {
   std::lock_guard<std::mutex> g(g_state_mu);
   int keep = 0;  // pairs whose end has not been reached yet (another thread's stream) stay pending
   for (int i = 0; i < g_prof.pending; ++i) {
@@ -90,7 +93,9 @@ void prof_collect(uint32_t radix_live) {
       continue;
     }
     int c = g_prof.cls[i];
-    if (c == kKRadix && !((radix_live >> g_prof.digit[i]) & 1u)) c = kKRadixSkipped;
+    if (c == kKRadix && (!((radix_live >> g_prof.digit[i]) & 1u) || sort_mode)) c = kKRadixSkipped;
+    if (c == kKMsd && sort_mode < g_prof.digit[i]) c = kKRadixSkipped;  // stage 2 runs in modes 2, 3; stage 3 in 3
+    if (c == kKLocal && sort_mode == 0) c = kKRadixSkipped;
     g_prof.launches[c]++;
     g_prof.ms[c] += ms;
     g_prof.alg_bytes[c] += c == kKRadixSkipped ? 0.0 : g_prof.bytes[i];
@@ -112,6 +117,7 @@ struct Plan {
   // workspace offsets
   size_t off_ctrl = 0, off_rec[2] = {0, 0}, off_tag[2] = {0, 0}, off_status = 0;
   size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, off_ord = 0, off_load = 0, total = 0;
+  size_t off_joint = 0, off_gstart = 0, off_rlist = 0, off_first = 0, off_meta = 0, off_spill = 0;
   uint64_t orp_tiles = 0, radix_tiles = 0;
 };
 
@@ -379,7 +385,15 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
     pl->off_tmp = off;     off = align256(off + n * pl->R);
     pl->off_hist = off;    off = align256(off + pl->digits * 256 * 4);
     pl->off_dbase = off;   off = align256(off + pl->digits * 256 * 8);
-    pl->off_rstatus = off; off = align256(off + pl->radix_tiles * 256 * 8);
+    // look-back words: the LSD passes' tiles, or the hybrid sort's second partition (whose tiles
+    // restart at every top-digit bucket: at most 256 more)
+    pl->off_rstatus = off; off = align256(off + (pl->radix_tiles + 256) * 256 * 8);
+    pl->off_joint = off;   off = align256(off + 65536 * 4);
+    pl->off_gstart = off;  off = align256(off + 65537 * 8);
+    pl->off_rlist = off;   off = align256(off + 65537 * 4);
+    pl->off_first = off;   off = align256(off + 257 * 8);
+    pl->off_meta = off;    off = align256(off + 16);
+    pl->off_spill = off;   off = align256(off + hybrid_spill_bytes(n, pl->R));
   }
   pl->total = off;
   return BOS_OK;
@@ -457,6 +471,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     info->max_cluster = 1;
     info->max_k = 0;
     info->stream_passes = 0;
+    info->sort_mode = 0;
     for (uint32_t x = 0; x < pl.npass; ++x) {
       info->stream_passes += pl.pass_stream[x] ? 1u : 0u;
       info->max_cluster = pl.pass_C[x] > info->max_cluster ? pl.pass_C[x] : info->max_cluster;
@@ -523,18 +538,45 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     ra.ctrl = ctrl;
     ra.ticket_base = 1;
   }
+  // the hybrid radix sort (partitions on the top digits, then on-chip sorts) unless the LSD sort
+  // is asked for; its plan kernel picks the LSD passes by itself when a group is too large
+  const bool hybrid = sort && !merge && !(p->flags & BOS_FLAG_LSD_SORT);
+  HybridArgs ha{};
+  if (hybrid) {
+    ha.in = d_in;
+    ha.buf0 = d_out;
+    ha.buf1 = ws + pl.off_tmp;
+    ha.n = n;
+    ha.hist = ra.hist;
+    ha.dbase = ra.dbase;
+    ha.joint = (uint32_t*)(ws + pl.off_joint);
+    ha.gstart = (unsigned long long*)(ws + pl.off_gstart);
+    ha.rlist = (uint32_t*)(ws + pl.off_rlist);
+    ha.first = (unsigned long long*)(ws + pl.off_first);
+    ha.meta = (uint32_t*)(ws + pl.off_meta);
+    ha.status = ra.status;
+    ha.scratch = (unsigned char*)(ws + pl.off_spill);
+    ha.local_ctas = hybrid_local_ctas(n, pl.R);
+    ha.ctrl = ctrl;
+  }
 
   for (uint32_t attempt = 0; attempt < max_attempts; ++attempt) {
     BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
     BOS_CUDA(cudaMemsetAsync(ws + pl.off_status, 0, pl.orp_tiles * 8, st));
     if (sort && !merge) {
       BOS_CUDA(cudaMemsetAsync(ra.hist, 0, pl.digits * 256 * 4, st));
-      BOS_CUDA(cudaMemsetAsync(ra.status, 0, pl.radix_tiles * 256 * 8, st));
+      BOS_CUDA(cudaMemsetAsync(ra.status, 0, (pl.radix_tiles + (hybrid ? 256 : 0)) * 256 * 8, st));
       int ev = prof_begin(st, kKHist, (double)n * pl.key_bytes);
-      BOS_CUDA(launch_radix_hist(ra, pl.R, st));
+      if (hybrid) {
+        BOS_CUDA(cudaMemsetAsync(ha.joint, 0, 65536 * 4, st));
+        BOS_CUDA(launch_hybrid(ha, pl.R, 0, st));
+      } else {
+        BOS_CUDA(launch_radix_hist(ra, pl.R, st));
+      }
       prof_end(ev, st);
       ev = prof_begin(st, kKPrep, 0.0);
       BOS_CUDA(launch_radix_prep(ra, pl.R, st));
+      if (hybrid) BOS_CUDA(launch_hybrid(ha, pl.R, 1, st));
       prof_end(ev, st);
     }
     if (oblivious) {
@@ -620,21 +662,30 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     if (merge)
       BOS_CUDA(launch_merge_sort(merge_first, d_out, ws + pl.off_tmp, n, pl.R, (uint64_t*)(ws + pl.off_rstatus), st,
                                  hooks));
-    else if (sort)
-      for (uint32_t d = 0; d < pl.digits; ++d) {
+    else if (sort) {
+      if (hybrid)  // each stage returns at once unless the plan's mode runs it
+        for (int stage = 2; stage <= 4; ++stage) {
+          const int ev = prof_begin(st, stage == 4 ? kKLocal : kKMsd, 2.0 * n * pl.R, (uint32_t)stage);
+          BOS_CUDA(launch_hybrid(ha, pl.R, stage, st));
+          prof_end(ev, st);
+        }
+      for (uint32_t d = 0; d < pl.digits; ++d) {  // skipped when the hybrid sort runs
         const int ev = prof_begin(st, kKRadix, 2.0 * n * pl.R, d);
         BOS_CUDA(launch_radix_pass(ra, pl.R, d, st));
         prof_end(ev, st);
       }
+    }
     Ctrl h{};
     BOS_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     BOS_CUDA(cudaStreamSynchronize(st));
-    if (g_prof.on) prof_collect(h.radix_live);
+    if (g_prof.on) prof_collect(h.radix_live, h.sort_mode);
     if (info) {
       info->attempts = attempt + 1;
-      info->radix_passes = (uint32_t)__builtin_popcount(h.radix_live);
+      info->sort_mode = h.sort_mode;
+      info->radix_passes = h.sort_mode ? h.sort_mode : (uint32_t)__builtin_popcount(h.radix_live);
     }
     if (h.timeout) return BOS_ERR_TIMEOUT;
+    if (h.bad) return BOS_ERR_CUDA;
     if (h.overflow || attempt < forced) continue;
     return BOS_OK;
   }
@@ -1450,7 +1501,7 @@ uint32_t bos_profile_read(bos_kernel_stat* out, uint32_t max, uint64_t* total_la
     std::unique_lock<std::mutex> g(g_state_mu);
     for (int i = 0; i < g_prof.pending; ++i) cudaEventSynchronize(g_prof.ev[2 * i + 1]);
   }
-  prof_collect(0xFFFFFFFFu);
+  prof_collect(0xFFFFFFFFu, 0u);
   std::lock_guard<std::mutex> g(g_state_mu);
   if (total_launches) *total_launches = g_prof.total_launches;
   uint32_t m = 0;

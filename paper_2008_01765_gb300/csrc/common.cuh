@@ -121,9 +121,18 @@ struct Ctrl {
   uint32_t timeout;          // a bounded wait gave up
   uint32_t forced;           // debug: attempts still to be reported as overflowed
   uint32_t radix_live;       // bit d set: digit d of the keys is not constant (a radix pass runs)
-  uint32_t tickets[60];      // dynamic work counters, one per launch that orders its CTAs
+  uint32_t sort_mode;        // sort after the ORP: 0 = LSD radix passes, m = 1..3: the hybrid sort's m passes
+  uint32_t bad;              // a device-side consistency check failed (the work it guards was skipped)
+  uint32_t tickets[58];      // dynamic work counters, one per launch that orders its CTAs
 };
 static_assert(sizeof(Ctrl) == 256, "control block size");
+
+// The LAST ORP pass writes the sort's scratch buffer (instead of the output) when an odd number of
+// sort passes follows it, so that the last sort pass writes the output.
+__device__ __forceinline__ bool sort_passes_odd(const Ctrl* c) {
+  const uint32_t p = c->sort_mode ? c->sort_mode : (uint32_t)__popc(c->radix_live);
+  return (p & 1u) != 0;
+}
 
 // Bounded spin: number of polls before a wait gives up (~0.5 s with the back-off below).
 constexpr uint32_t kSpinLimit = 1u << 22;

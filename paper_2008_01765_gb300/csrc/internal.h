@@ -129,6 +129,32 @@ struct RadixArgs {
   uint32_t ticket_base;
 };
 uint64_t radix_tiles(uint64_t n, int R);
+
+// Hybrid radix sort (sort_hybrid.cu): MSD partitions on the top one or two digits, then an on-chip
+// sort of every range of groups; falls back to the LSD passes (ctrl->sort_mode = 0) when a group
+// exceeds hybrid_cap(R) records. stage: 0 histogram (hist and joint), 1 plan, 2 partition by the
+// top varying digit, 3 partition by the next one inside every bucket, 4 the on-chip sort.
+struct HybridArgs {
+  const void* in;                   // histogram source (the ORP's input: the same multiset of keys)
+  void* buf0;                       // final output
+  void* buf1;                       // scratch of n records
+  uint64_t n;
+  uint32_t* hist;                   // [digits][256] digit counts (shared with the LSD path)
+  const unsigned long long* dbase;  // [digits][256] exclusive digit offsets (radix prep)
+  uint32_t* joint;                  // [65536] counts of the top two digits
+  unsigned long long* gstart;       // [65537] group starts
+  uint32_t* rlist;                  // [65537] first group of every range
+  unsigned long long* first;        // [257] partition tiles before every top-digit bucket
+  uint32_t* meta;                   // [4] mode, top varying digit, next varying digit, ranges
+  unsigned long long* status;       // look-back words for radix_tiles(n) + 256 tiles
+  unsigned char* scratch;           // hybrid_spill_bytes(n, R): one spill buffer per on-chip-sort CTA
+  uint32_t local_ctas;              // = hybrid_local_ctas(n, R)
+  Ctrl* ctrl;
+};
+uint32_t hybrid_cap(int R);
+uint32_t hybrid_local_ctas(uint64_t n, int R);
+size_t hybrid_spill_bytes(uint64_t n, int R);
+cudaError_t launch_hybrid(const HybridArgs& a, int R, int stage, cudaStream_t st);
 // Radix stages over many arrays in one launch (batched sort).
 struct BatchRadix {
   const RadixArgs* args;  // device: one entry per array

@@ -316,7 +316,7 @@ __global__ void obl_strip_kernel(ObliviousArgs a, uint32_t src) {
   using Rec = typename RecT<R>::T;
   const Rec* brec = reinterpret_cast<const Rec*>(a.rec[src]);
   Rec* out = reinterpret_cast<Rec*>(a.out0);
-  if (a.out_sel && (__popc(a.ctrl->radix_live) & 1)) out = reinterpret_cast<Rec*>(a.out1);
+  if (a.out_sel && sort_passes_odd(a.ctrl)) out = reinterpret_cast<Rec*>(a.out1);
   const uint32_t out_buf = (out == reinterpret_cast<Rec*>(a.out0)) ? kBufOut : kBufTmp;
   const uint32_t bufr = src ? kBufRecB : kBufRecA;
   for (uint64_t b = blockIdx.x; b < a.B; b += gridDim.x) {

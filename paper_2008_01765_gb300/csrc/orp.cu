@@ -306,7 +306,7 @@ __device__ __forceinline__ void orp_pass_body(const PassArgs& a, uint64_t q) {
     const uint64_t prefix = (uint64_t)misc[1] | ((uint64_t)misc[2] << 32);
     const uint32_t total = moff[D];
     Rec* out = reinterpret_cast<Rec*>(a.out0);
-    if (a.out_sel && (__popc(a.ctrl->radix_live) & 1)) out = reinterpret_cast<Rec*>(a.out1);
+    if (a.out_sel && sort_passes_odd(a.ctrl)) out = reinterpret_cast<Rec*>(a.out1);
     const uint32_t out_buf = (out == reinterpret_cast<Rec*>(a.out0)) ? kBufOut : kBufTmp;
     for (uint32_t j = tid; j < total; j += kThreads) {
       // bucket u with moff[u] <= j < moff[u+1] (binary search over D+1 offsets)

@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(kT, 1) orp_fast_kernel(PassArgs a, uint32_t C)
       __syncthreads();
       const uint64_t gofs = *reinterpret_cast<unsigned long long*>(misc + kMiscPrefix) + misc[kMiscBefore];
       Rec* out = reinterpret_cast<Rec*>(a.out0);
-      if (a.out_sel && (__popc(a.ctrl->radix_live) & 1)) out = reinterpret_cast<Rec*>(a.out1);
+      if (a.out_sel && sort_passes_odd(a.ctrl)) out = reinterpret_cast<Rec*>(a.out1);
       const uint32_t out_buf = (out == reinterpret_cast<Rec*>(a.out0)) ? kBufOut : kBufTmp;
       for (uint32_t c = warp; c < nch; c += kW) {
         const uint32_t up = c / cpb, m = min(tot[crank * Dc + up], Z);

@@ -621,3 +621,83 @@ def test_out_of_core_orp_equals_in_memory(bos, G, n, Z, rec_bytes):
     np.testing.assert_array_equal(got, ref)
     alone, _ = gpu_orp(bos, recs, Z, seed, max_attempts=16)
     np.testing.assert_array_equal(got, alone)
+
+
+def _hybrid_keys(n, rec_bytes, recipe, seed):
+    """Records whose keys steer the hybrid sort's plan (shaped from the seeded generators)."""
+    if recipe in inputs.DISTRIBUTIONS:
+        return inputs.make_records(n, rec_bytes, recipe, seed=seed)
+    recs = inputs.make_records(n, rec_bytes, "uniform", seed=seed)
+    kt = recs.dtype["key"].type
+    bits = recs.dtype["key"].itemsize * 8
+    k = recs["key"].copy()
+    if recipe == "low16_zero":  # digits 0 and 1 constant: the on-chip sort starts at digit 2
+        k &= kt(~np.uint64(0xFFFF) & np.uint64((1 << bits) - 1))
+    elif recipe == "top_two_values":  # top digit: 2 values over n/2 records each, next digit constant
+        top = np.where(np.arange(n) % 2 == 0, 1, 2).astype(np.uint64) << np.uint64(bits - 8)
+        k = ((k.astype(np.uint64) & np.uint64((1 << (bits - 24)) - 1)) | top).astype(kt)
+    elif recipe == "half_equal":  # half the keys one value: a group larger than any range
+        k[::2] = kt(12345)
+    elif recipe == "d6_few":  # digit 6 takes 16 values: on-chip sub-buckets too large for a warp
+        sh = np.uint64(bits - 16)
+        k64 = k.astype(np.uint64)
+        k = ((k64 & ~(np.uint64(0xFF) << sh)) | (((k64 >> sh) & np.uint64(0x0F)) << sh)).astype(kt)
+    elif recipe == "few_values":  # 64 distinct keys: whole ranges of equal keys
+        table = inputs.make_records(64, rec_bytes, "uniform", seed=seed + 1)["key"]
+        k = table[np.arange(n) % 64]
+    recs["key"] = k
+    return recs
+
+
+HYBRID_CAP = {16: 19456, 8: 28672}  # records one CTA sorts on chip (sort_hybrid.cu)
+
+
+def _hybrid_mode(keys, rec_bytes):
+    """The plan's rule stated on the keys: 1 if all fit one CTA, 2 if every bucket of the top
+    varying digit does, 3 if the top two digits both vary and every pair of them does, else 0."""
+    n, cap, D = keys.size, HYBRID_CAP[rec_bytes], rec_bytes // 2
+    k = keys.astype(np.uint64)
+    digit = [(k >> np.uint64(8 * d)) & np.uint64(255) for d in range(D)]
+    live = [d for d in range(D) if np.bincount(digit[d].astype(np.int64), minlength=256).max() < n]
+    if n < 2 or not live:
+        return 0
+    if n <= cap:
+        return 1
+    dA = live[-1]
+    if np.bincount(digit[dA].astype(np.int64), minlength=256).max() <= cap:
+        return 2
+    if len(live) >= 2 and dA == D - 1 and live[-2] == D - 2:
+        pair = (digit[D - 1] << np.uint64(8)) | digit[D - 2]
+        if np.bincount(pair.astype(np.int64), minlength=65536).max() <= cap:
+            return 3
+    return 0
+
+
+HYBRID_CASES = [
+    # (n, rec_bytes, keys, sort_mode the plan must pick)
+    (1, 16, "uniform", 0), (2, 16, "uniform", 1), (33, 8, "uniform", 1), (10000, 16, "dup1024", 1),
+    (19456, 16, "uniform", 1), (19457, 16, "uniform", 2), (28672, 8, "uniform", 1), (28673, 8, "reverse", 2),
+    (1 << 20, 16, "uniform", 2), (1 << 20, 8, "uniform", 2), ((1 << 22) + 5, 16, "uniform", 2),
+    (1 << 23, 16, "uniform", 3), ((1 << 23) - 7, 8, "uniform", 3), (1 << 20, 16, "dup1024", 2),
+    (1 << 20, 16, "sorted", 2), (1 << 20, 16, "reverse", 0), (200003, 16, "equal", 0),
+    (1 << 20, 16, "low16_zero", 2), (1 << 20, 16, "top_two_values", 0), (1 << 20, 8, "half_equal", 0),
+    (1 << 20, 16, "few_values", None), (1 << 22, 16, "d6_few", 2), (1 << 24, 8, "uniform", 3),
+]
+
+
+@pytest.mark.parametrize("n,rec_bytes,keys,mode", HYBRID_CASES)
+def test_hybrid_sort_matches_oracle_and_lsd(bos, n, rec_bytes, keys, mode):
+    # The hybrid radix sort (the default) and the LSD radix sort both give the oracle's stable
+    # sort of the ORP output; the plan's mode is the one the key distribution calls for.
+    recs = _hybrid_keys(n, rec_bytes, keys, seed=n % 1000 + rec_bytes)
+    Z = 512
+    ref, rinfo = oracle.sort(recs, Z, 21, method=oracle.CLOSED)
+    got, info = gpu_sort(bos, recs, Z, 21)
+    assert info.sort_mode == _hybrid_mode(recs["key"], rec_bytes)
+    if mode is not None:
+        assert info.sort_mode == mode
+    assert info.attempts == rinfo.attempts
+    np.testing.assert_array_equal(got, ref)
+    lsd, linfo = gpu_sort(bos, recs, Z, 21, flags=bos.FLAG_LSD_SORT)
+    assert linfo.sort_mode == 0
+    np.testing.assert_array_equal(lsd, ref)
