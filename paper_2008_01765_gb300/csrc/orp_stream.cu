@@ -7,11 +7,13 @@
 //
 // The persistent-cluster kernel (orp_fast.cu) holds all 2^k output buckets on chip, which caps k
 // by shared memory. This kernel streams instead: one CTA takes a whole subproblem and reads its
-// input buckets in order, each one (a "batch"; in the first pass, two groups of input records)
-// brought in by TMA bulk copies through a three-stage ring. Every output bucket owns a small ring
-// of kRing slots in shared memory; a real is appended to its bucket's ring at its stable rank, and
-// whenever a ring holds a whole chunk of kChunk slots the chunk leaves for HBM (coalesced 16-byte
-// stores). At the end of the subproblem every bucket's last partial chunk is padded with dummies
+// input in order, in batches brought in by TMA bulk copies through a ring of stages: in the first
+// pass a batch is two groups of input records (three stages); in a middle pass it is two input
+// buckets (four one-bucket stages) when they fit, else one (three stages), so that the per-batch
+// work (barriers, flushes, counter upkeep) is shared by about Z reals. Every output bucket owns a
+// small ring of kRing slots in shared memory; a real is appended to its bucket's ring at its
+// stable rank, and whenever a ring holds a whole chunk of kChunk slots the chunk leaves for HBM
+// (coalesced 16-byte stores). At the end of the subproblem every bucket's last partial chunk is padded with dummies
 // and its remaining chunks are written as dummies. So shared memory bounds the chunk buffers, not
 // the subproblem, and one pass applies up to 9 levels with no cluster.
 //
@@ -42,20 +44,26 @@ constexpr int kSW = kST / 32;
 constexpr uint32_t kChunk = 8;         // slots per HBM write (128 B of 16-byte records)
 constexpr uint32_t kRing = 24;         // ring slots per output bucket
 constexpr uint32_t kRingStride = 25;   // ring pitch in shared memory (odd: spreads the banks)
-constexpr uint32_t kStages = 3;        // input batches in flight
+constexpr uint32_t kStages = 3;        // input stages (first pass: batches; middle: buckets)
+constexpr uint32_t kStagesPaired = 4;  // middle pass taking two input buckets per batch
+constexpr uint32_t kSmemLimit = 232448 - 1024;  // opt-in shared memory per CTA less static use
 constexpr uint32_t kMaxItems = 2;      // slots per thread per batch: Z <= 2048
 constexpr uint32_t kSub = 16;          // slots per round when a batch is redone (7 + 16 <= kRing)
 constexpr uint32_t kMinK = 5, kMaxK = 9;
 
 struct StreamLayout {
   uint32_t ring_rec, ring_tag, aux, stage, stage_bytes, fill, done, cnt, lv, misc, total;
+  uint32_t stages, pair;  // input stages; middle pass: two input buckets per batch (pair = 1)
 };
 
 __host__ __device__ inline uint32_t st_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_t k, bool first) {
+__host__ __device__ inline StreamLayout stream_layout_n(int R, uint32_t Z, uint32_t k, bool first, uint32_t stages,
+                                                        uint32_t pair) {
   const uint32_t D = 1u << k;
   StreamLayout l{};
+  l.stages = stages;
+  l.pair = pair;
   uint32_t off = 0;
   l.ring_rec = off;
   off = st_align(off + D * kRingStride * R, 16);
@@ -63,10 +71,11 @@ __host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_
   off = st_align(off + D * kRingStride * 4, 16);
   l.aux = off;
   off = st_align(off + D * kRingStride * 2, 16);
-  // first pass: up to Z input records (two groups of at most Z/2) plus one record of alignment
+  // first pass: up to Z input records (two groups of at most Z/2) plus one record of alignment;
+  // middle pass: one input bucket (tags, then records)
   l.stage_bytes = first ? st_align((Z + 2) * R, 128) : st_align(Z * (4 + R), 128);
   l.stage = st_align(off, 128);
-  off = l.stage + kStages * l.stage_bytes;
+  off = l.stage + stages * l.stage_bytes;
   l.fill = off;
   off += D * 4;
   l.done = off;
@@ -79,6 +88,16 @@ __host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_
   off = l.misc + 64;
   l.total = off;
   return l;
+}
+
+// The middle pass takes two input buckets per batch (four single-bucket stages) when Z fits one
+// item per thread per bucket and the stages fit; otherwise one bucket per batch, three stages.
+__host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_t k, bool first) {
+  if (!first && Z <= (uint32_t)kST) {
+    const StreamLayout p = stream_layout_n(R, Z, k, false, kStagesPaired, 1);
+    if (p.total <= kSmemLimit) return p;
+  }
+  return stream_layout_n(R, Z, k, first, kStages, 0);
 }
 
 template <int R, bool FIRST, bool TRACE>
@@ -95,14 +114,19 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
   uint32_t* done = reinterpret_cast<uint32_t*>(smem + lay.done);  // chunks written per bucket
   uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + lay.cnt);    // [2][D] reals per round
   uint32_t* lv = reinterpret_cast<uint32_t*>(smem + lay.lv);      // level l, prefix p: lv[2^l - 2 + p]
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + lay.misc);  // [kStages]
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + lay.misc);  // [lay.stages]
   volatile uint32_t* flag = reinterpret_cast<volatile uint32_t*>(smem + lay.misc + 32);  // [2]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t nsub = a.B >> k;
-  const uint32_t NB = FIRST ? D / 2 : D;  // batches per subproblem
+  // units: what one stage holds (first pass: a batch of two groups; middle pass: one input
+  // bucket); a batch is one unit, or two input buckets when the middle pass is paired
+  const uint32_t NU = FIRST ? D / 2 : D;  // units per subproblem
+  const uint32_t upb = (!FIRST && lay.pair) ? 2u : 1u;
+  const uint32_t NB = NU / upb;  // batches per subproblem
+  const uint32_t nst = lay.stages;
   const uint64_t mysub = blockIdx.x < nsub ? (nsub - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const uint64_t nbatch = mysub * NB;
+  const uint64_t nbatch = mysub * NB, nunits = mysub * NU;
   const Rec* in_first = reinterpret_cast<const Rec*>(a.in);
   const Rec* in_rec = reinterpret_cast<const Rec*>(a.in_rec);
   Rec* out_rec = reinterpret_cast<Rec*>(a.out_rec);
@@ -116,7 +140,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     lv[x] = 0;
   }
   if (tid == 0) {
-    for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(bars + s), 1);
+    for (uint32_t s = 0; s < nst; ++s) mbar_init(smem_u32(bars + s), 1);
     flag[0] = flag[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -213,32 +237,36 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     }
   };
 
-  // Batch cursor (q, s) with its stage st and mbarrier parity par, advanced without division;
-  // thread 0 keeps a second cursor kStages batches ahead for the TMA issue.
+  // Unit cursor (q, unit, stage), advanced without division; thread 0 keeps it nst units ahead
+  // of the batches for the TMA issue.
   uint64_t iq = blockIdx.x;
   uint32_t is = 0, ist = 0;
   uint64_t issued = 0;
   auto issue_next = [&]() {
     issue(iq, is, ist);
     ++issued;
-    if (++is == NB) {
+    if (++is == NU) {
       is = 0;
       iq += gridDim.x;
     }
-    if (++ist == kStages) ist = 0;
+    if (++ist == nst) ist = 0;
   };
   if (tid == 0)
-    while (issued < kStages && issued < nbatch) issue_next();
+    while (issued < nst && issued < nunits) issue_next();
 
   uint64_t q = blockIdx.x;
-  uint32_t s = 0, st = 0, par = 0;
+  uint32_t s = 0, st = 0, par = 0;  // batch s of subproblem q; stage and parity of its first unit
   for (uint64_t g = 0; g < nbatch; ++g) {
     const uint32_t pb = (uint32_t)(g & 1);
+    const uint32_t st1 = st + 1 == nst ? 0u : st + 1, par1 = st + 1 == nst ? par ^ 1u : par;
     unsigned char* stg = smem + lay.stage + st * lay.stage_bytes;
+    unsigned char* stg1 = smem + lay.stage + st1 * lay.stage_bytes;  // paired: the second bucket
     const uint32_t* stag = reinterpret_cast<const uint32_t*>(stg);
+    const uint32_t* stag1 = reinterpret_cast<const uint32_t*>(stg1);
     Rec* srec = reinterpret_cast<Rec*>(FIRST ? stg : stg + Z * 4);
+    Rec* srec1 = reinterpret_cast<Rec*>(stg1 + Z * 4);
     uint64_t lo = 0, hi = 0;
-    uint32_t nslot = Z, soff = 0;
+    uint32_t nslot = upb * Z, soff = 0;
     if constexpr (FIRST) {
       first_range(q, s, lo, hi);
       nslot = (uint32_t)(hi - lo);
@@ -254,6 +282,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
       }
     } else {
       mbar_wait(smem_u32(bars + st), par, a.ctrl);
+      if (upb == 2) mbar_wait(smem_u32(bars + st1), par1, a.ctrl);
     }
     const uint64_t obase = q * D;
     uint32_t* cntp = cnt + pb * D;
@@ -273,7 +302,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
           if constexpr (FIRST)
             tg = label_of(lo + x, a.seed, a.attempt, L);
           else
-            tg = stag[x];
+            tg = x < Z ? stag[x] : stag1[x - Z];  // paired: slots Z.. are the second bucket's
           itg[j] = tg;
           if (tg != kDummy) {
             const uint32_t u = (tg >> shift) & (D - 1);
@@ -304,7 +333,7 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
           if (c > 1)
             for (uint32_t cc = 0; cc < c; ++cc) r += aux[u * kRingStride + (f + cc) % kRing] < x ? 1u : 0u;
           const uint32_t pos = u * kRingStride + (f + r) % kRing;
-          ring_rec[pos] = srec[soff + x];
+          ring_rec[pos] = (FIRST || x < Z) ? srec[soff + x] : srec1[x - Z];
           ring_tag[pos] = itg[j];
           if (r == 0) fill[u] = f + c;
         }
@@ -339,10 +368,12 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     // ---- after the batch: its stage is free; level blocks that end here are checked ----
     if (tid == 0) {
       flag[pb] = 0u;
-      if (issued < nbatch) issue_next();
+      for (uint32_t x = 0; x < upb; ++x)
+        if (issued < nunits) issue_next();
     }
-    {  // level l's blocks end after every 2^l batches (2^(l-1) in the first pass): its 2^l counters
-      const uint32_t e = FIRST ? __ffs(~s) : __ffs(~s) - 1;  // levels 1..e end here
+    {  // level l's blocks end after every 2^l input buckets: 2^(l-1) batches of two (first pass,
+      // paired middle pass), 2^l batches of one
+      const uint32_t e = (FIRST || upb == 2) ? __ffs(~s) : __ffs(~s) - 1;  // levels 1..e end here
       const uint32_t lmax = e < k - 1 ? e : k - 1;
       for (uint32_t t = tid; t + 2 < (2u << lmax); t += kST) {
         if (lv[t] > Z) atomicExch(&a.ctrl->overflow, 1u);
@@ -379,10 +410,11 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
       s = 0;
       q += gridDim.x;
     }
-    if (++st == kStages) {
-      st = 0;
-      par ^= 1u;
-    }
+    for (uint32_t x = 0; x < upb; ++x)
+      if (++st == nst) {
+        st = 0;
+        par ^= 1u;
+      }
   }
 }
 

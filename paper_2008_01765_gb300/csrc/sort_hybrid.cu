@@ -324,39 +324,39 @@ __device__ __forceinline__ void local_scan(uint32_t* wc, uint32_t* half, uint32_
   __syncthreads();
 }
 
-// Ascending bitonic sort of the s <= 32 * EPL words at base, in registers (element r * 32 + lane
-// of lane `lane`; the positions past s hold the largest word, which no entry equals).
+// Ascending bitonic sort of the s <= 32 * EPL words at base, in registers: lane l holds elements
+// l * EPL .. l * EPL + EPL - 1, so the stages with partner distance below EPL stay in registers.
+// Positions past s hold the largest word, which no entry equals (entries are distinct).
 template <typename W, int EPL>
 __device__ __forceinline__ void warp_sort(W* base, uint32_t s, uint32_t lane) {
   W v[EPL];
 #pragma unroll
   for (int r = 0; r < EPL; ++r) {
-    const uint32_t e = r * 32 + lane;
+    const uint32_t e = lane * EPL + r;
     v[r] = e < s ? base[e] : ~W(0);
   }
 #pragma unroll
   for (int kk = 2; kk <= 32 * EPL; kk <<= 1) {
 #pragma unroll
     for (int j = kk >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {  // partners in the same lane: elements r and r + j / 32
-        const int jr = j >> 5;
+      if (j < EPL) {  // partners in the same lane: elements r and r ^ j
 #pragma unroll
         for (int r = 0; r < EPL; ++r) {
-          if ((r & jr) == 0) {
-            const bool up = ((r * 32) & kk) == 0;
-            const W x = v[r], y = v[r | jr];
-            const bool sw = up ? (y < x) : (x < y);
+          if ((r & j) == 0) {
+            const bool up = ((lane * EPL + (uint32_t)r) & (uint32_t)kk) == 0;
+            const W x = v[r], y = v[r | j];
+            const bool sw = (y < x) == up;
             v[r] = sw ? y : x;
-            v[r | jr] = sw ? x : y;
+            v[r | j] = sw ? x : y;
           }
         }
-      } else {  // partners in lane ^ j
+      } else {  // partners in lane ^ (j / EPL), same r
+        const uint32_t lj = (uint32_t)j / EPL;
 #pragma unroll
         for (int r = 0; r < EPL; ++r) {
-          const W o = __shfl_xor_sync(0xFFFFFFFFu, v[r], j);
-          const bool up = (((uint32_t)r * 32 + lane) & (uint32_t)kk) == 0;
-          const bool keep_min = ((lane & (uint32_t)j) == 0) == up;
-          // the words are distinct, so o < v decides both min and max
+          const W o = __shfl_xor_sync(0xFFFFFFFFu, v[r], lj);
+          const bool up = ((lane * EPL + (uint32_t)r) & (uint32_t)kk) == 0;
+          const bool keep_min = ((lane & lj) == 0) == up;
           if ((o < v[r]) == keep_min) v[r] = o;
         }
       }
@@ -364,20 +364,26 @@ __device__ __forceinline__ void warp_sort(W* base, uint32_t s, uint32_t lane) {
   }
 #pragma unroll
   for (int r = 0; r < EPL; ++r) {
-    const uint32_t e = r * 32 + lane;
+    const uint32_t e = lane * EPL + r;
     if (e < s) base[e] = v[r];
   }
 }
 
-// Per-warp counts of digit d of the keys at positions [wlo, whi) (rows of 32; SK holds the keys).
-template <typename Key>
-__device__ __forceinline__ void local_count(const Key* SK, uint32_t* wc, uint32_t d, uint32_t wlo, uint32_t whi,
-                                            uint32_t lane, uint32_t warp, uint32_t lt_mask) {
+// Lanes of the warp with this lane's digit value (0..255, or 256 = no item). A full row of the
+// warp has no empty lane, so eight ballots decide it.
+__device__ __forceinline__ uint32_t row_peers(uint32_t dg, bool full) {
+  return full ? ballot_peers(dg, 8) : ballot_peers(dg, 9);
+}
+
+// Per-warp counts of digit d of the keys at positions [wlo, whi) (rows of 32).
+template <int R>
+__device__ __forceinline__ void local_count(const typename RecT<R>::T* in, uint32_t* wc, uint32_t d, uint32_t wlo,
+                                            uint32_t whi, uint32_t lane, uint32_t warp, uint32_t lt_mask) {
   for (uint32_t b = wlo; b < whi; b += 32) {
     const uint32_t j = b + lane;
     const bool valid = j < whi;
-    const uint32_t dg = valid ? (uint32_t)((SK[j] >> (8 * d)) & 255u) : 256u;
-    const uint32_t peers = ballot_peers(dg, 9);
+    const uint32_t dg = valid ? (uint32_t)((load_key<R>(in + j) >> (8 * d)) & 255u) : 256u;
+    const uint32_t peers = row_peers(dg, b + 32 <= whi);
     if (valid && (peers & lt_mask) == 0) wc[warp * 257 + dg] += __popc(peers);
     __syncwarp();
   }
@@ -441,8 +447,7 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
     uint32_t* wn = WC + kLWarps * 257;
     for (uint32_t x = tid; x < kLWarps * 257; x += kLThreads) wc[x] = 0;
     __syncthreads();
-    // read 1: keys and positions into shared memory, the key AND / OR over the range, and each
-    // warp's counts of digit dspec
+    // read 1: the key AND / OR over the range, and each warp's counts of digit dspec
     Key kand = ~Key(0), kor = Key(0);
     for (uint32_t b0 = wlo; b0 < whi; b0 += 32 * kU) {
       Key kk[kU];
@@ -457,13 +462,11 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
         const uint32_t j = b0 + u * 32 + lane;
         const bool valid = j < whi;
         if (valid) {
-          SK[j] = kk[u];
-          SI[j] = (uint16_t)j;
           kand &= kk[u];
           kor |= kk[u];
         }
         const uint32_t dg = valid ? (uint32_t)((kk[u] >> (8 * dspec)) & 255u) : 256u;
-        const uint32_t peers = ballot_peers(dg, 9);
+        const uint32_t peers = row_peers(dg, b0 + u * 32 + 32 <= whi);
         if (valid && (peers & lt_mask) == 0) wc[warp * 257 + dg] += __popc(peers);
         __syncwarp();
       }
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
       if (dC != counted) {
         for (uint32_t x = tid; x < kLWarps * 257; x += kLThreads) wc[x] = 0;
         __syncthreads();
-        local_count(SK, wc, dC, wlo, whi, lane, warp, lt_mask);
+        local_count<R>(in, wc, dC, wlo, whi, lane, warp, lt_mask);
         __syncthreads();
         counted = dC;
       }
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
           const uint32_t j = b0 + u * 32 + lane;
           const bool valid = j < whi;
           const uint32_t dg = valid ? (uint32_t)((kk[u] >> (8 * dC)) & 255u) : 256u;
-          const uint32_t peers = ballot_peers(dg, 9);
+          const uint32_t peers = row_peers(dg, b0 + u * 32 + 32 <= whi);
           const uint32_t lt = __popc(peers & lt_mask);
           const uint32_t base = wc[warp * 257 + dg];
           __syncwarp();
@@ -576,14 +579,18 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
     // LSD passes over the varying digits. Pass q moves (key, position) from the shared buffers to
     // the spill buffers (q even) or back (q odd), stably by digit d, and counts the next digit for
     // the warp that will read each position.
+    for (uint32_t j = tid; j < m; j += kLThreads) {  // keys and positions into shared memory
+      SK[j] = load_key<R>(in + j);
+      SI[j] = (uint16_t)j;
+    }
     uint32_t d = (uint32_t)__ffs(vm) - 1;
     vm &= vm - 1;
     if (d != counted) {
       for (uint32_t x = tid; x < kLWarps * 257; x += kLThreads) wc[x] = 0;
       __syncthreads();
-      local_count(SK, wc, d, wlo, whi, lane, warp, lt_mask);
-      __syncthreads();
+      local_count<R>(in, wc, d, wlo, whi, lane, warp, lt_mask);
     }
+    __syncthreads();
     uint32_t q = 0;
     while (true) {
       const bool more = vm != 0;
@@ -611,7 +618,7 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
           if (b0 + u * 32 >= whi) break;
           const bool valid = b0 + u * 32 + lane < whi;
           const uint32_t dg = valid ? (uint32_t)((kk[u] >> (8 * d)) & 255u) : 256u;
-          const uint32_t peers = ballot_peers(dg, 9);
+          const uint32_t peers = row_peers(dg, b0 + u * 32 + 32 <= whi);
           const uint32_t lt = __popc(peers & lt_mask);
           const uint32_t base = wc[warp * 257 + dg];
           __syncwarp();
