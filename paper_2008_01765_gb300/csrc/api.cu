@@ -53,6 +53,23 @@ struct Prof {
 };
 Prof g_prof;
 
+// Zeroes bytes at p on stream st with a kernel. The library's workspace resets are kernels, not
+// cudaMemsetAsync: a memset can wait behind a large copy that another stream has in flight (the
+// next step's input or the previous step's output in a pipelined caller).
+__global__ void zero_kernel(unsigned char* p, size_t bytes) {
+  const size_t head0 = (16 - ((uintptr_t)p & 15)) & 15;
+  const size_t head = head0 < bytes ? head0 : bytes;
+  const size_t body = (bytes - head) / 16;
+  uint4* q = reinterpret_cast<uint4*>(p + head);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < body; i += (size_t)gridDim.x * blockDim.x)
+    q[i] = make_uint4(0, 0, 0, 0);
+  if (blockIdx.x == 0 && threadIdx.x < 16) {
+    if (threadIdx.x < head) p[threadIdx.x] = 0;
+    const size_t t = head + body * 16 + threadIdx.x;
+    if (t < bytes) p[t] = 0;
+  }
+}
+
 // Records an event pair around one launch when profiling is on. Returns the slot or -1.
 int prof_begin(cudaStream_t st, int cls, double bytes, uint32_t digit = 0) {
   g_prof.total_launches.fetch_add(1, std::memory_order_relaxed);
@@ -68,6 +85,15 @@ int prof_begin(cudaStream_t st, int cls, double bytes, uint32_t digit = 0) {
 }
 void prof_end(int i, cudaStream_t st) {
   if (i >= 0) cudaEventRecord(g_prof.ev[2 * i + 1], st);
+}
+cudaError_t zero_async(void* p, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  const size_t words = bytes / 16 + 1;
+  const size_t blocks = (words + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
+  g_prof.total_launches.fetch_add(1, std::memory_order_relaxed);
+  zero_kernel<<<grid, 256, 0, st>>>(static_cast<unsigned char*>(p), bytes);
+  return cudaGetLastError();
 }
 // Folds the finished event pairs into the per-class totals (the stream has been synchronised).
 // A launch that returned at once (a constant digit; the LSD passes when the hybrid sort ran; a
@@ -561,14 +587,14 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
   }
 
   for (uint32_t attempt = 0; attempt < max_attempts; ++attempt) {
-    BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-    BOS_CUDA(cudaMemsetAsync(ws + pl.off_status, 0, pl.orp_tiles * 8, st));
+    BOS_CUDA(zero_async(ctrl, sizeof(Ctrl), st));
+    BOS_CUDA(zero_async(ws + pl.off_status, pl.orp_tiles * 8, st));
     if (sort && !merge) {
-      BOS_CUDA(cudaMemsetAsync(ra.hist, 0, pl.digits * 256 * 4, st));
-      BOS_CUDA(cudaMemsetAsync(ra.status, 0, (pl.radix_tiles + (hybrid ? 256 : 0)) * 256 * 8, st));
+      BOS_CUDA(zero_async(ra.hist, pl.digits * 256 * 4, st));
+      BOS_CUDA(zero_async(ra.status, (pl.radix_tiles + (hybrid ? 256 : 0)) * 256 * 8, st));
       int ev = prof_begin(st, kKHist, (double)n * pl.key_bytes);
       if (hybrid) {
-        BOS_CUDA(cudaMemsetAsync(ha.joint, 0, 65536 * 4, st));
+        BOS_CUDA(zero_async(ha.joint, 65536 * 4, st));
         BOS_CUDA(launch_hybrid(ha, pl.R, 0, st));
       } else {
         BOS_CUDA(launch_radix_hist(ra, pl.R, st));
@@ -923,7 +949,7 @@ bos_status batch_build(const BatchIn& b, const BatchLayout& L, char* ws, const s
 }
 
 bos_status batch_enqueue(const BatchLayout& L, char* ws, const std::vector<BatchLaunch>& launches, cudaStream_t st) {
-  BOS_CUDA(cudaMemsetAsync(ws, 0, L.zero_end, st));
+  BOS_CUDA(zero_async(ws, L.zero_end, st));
   const bool trace = trace_snapshot().buf != nullptr;
   for (const BatchLaunch& l : launches) {
     if (l.kind == 0) {
@@ -1213,7 +1239,7 @@ bos_status bos_shard_local(const void* d_in, uint64_t n, uint32_t G, uint32_t r,
   Ctrl* ctrl = (Ctrl*)(ws + pl.off_ctrl);
   const uint64_t lo = ((uint64_t)r * sp.Bl * n) >> sp.L;
   const Trace tr = trace_snapshot();
-  BOS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  BOS_CUDA(zero_async(ctrl, sizeof(Ctrl), st));
   for (uint32_t x = 0; x < pl.npass; ++x) {
     PassArgs a{};
     const bool first = x == 0;
@@ -1268,8 +1294,8 @@ bos_status bos_shard_final(uint64_t n, uint32_t G, uint32_t r, const bos_params*
   const Trace tr = trace_snapshot();
   const uint64_t nsub = sp.Bl >> sp.g;
   // the local step's overflow flag stays; the tickets and look-back words start at zero
-  BOS_CUDA(cudaMemsetAsync(&ctrl->tickets[0], 0, sizeof(ctrl->tickets), st));
-  BOS_CUDA(cudaMemsetAsync(ws + pl.off_status, 0, nsub * 8, st));
+  BOS_CUDA(zero_async(&ctrl->tickets[0], sizeof(ctrl->tickets), st));
+  BOS_CUDA(zero_async(ws + pl.off_status, nsub * 8, st));
   PassArgs a{};
   a.in_rec = ws + sp.recv_rec;
   a.in_tag = (const uint32_t*)(ws + sp.recv_tag);
@@ -1396,7 +1422,7 @@ bos_status bos_orp_out_of_core(const void* h_in, void* h_out, uint64_t n, const 
                                    hs + r * per_rank + G * sp.chunk_rec + d * sp.chunk_tag, sp.chunk_tag,
                                    cudaMemcpyHostToDevice, st));
         }
-        BOS_CUDA(cudaMemsetAsync(d_ws + sp.lp.off_ctrl, 0, sizeof(Ctrl), st));
+        BOS_CUDA(zero_async(d_ws + sp.lp.off_ctrl, sizeof(Ctrl), st));
         uint64_t count = 0;
         uint32_t ovf = 0;
         if ((s = bos_shard_final(n, G, d, p, attempt, d_part, sp.Bl * p->Z, d_ws, ws_bytes, stream, &count, &ovf)) !=
