@@ -542,6 +542,11 @@ def main():
             def copy_in(s):
                 b0, b1 = tev(), tev()
                 with torch.cuda.stream(h2d):
+                    if s >= 2 and ev_out[s % 2] is not None:
+                        # after the read-back of step s - 2 (the previous D2H): the two copies
+                        # would share the host link, and the next sort starts only when that
+                        # read-back ends, so it should end as early as it can
+                        h2d.wait_event(ev_out[s % 2])
                     b0.record(h2d)
                     xin[s % 2].copy_(pin_in, non_blocking=True)
                     b1.record(h2d)
@@ -591,8 +596,8 @@ def main():
                        "h2d_ms": avg["h2d"], "d2h_ms": avg["d2h"], "sort_ms": avg["sort"],
                        "h2d_GBps": n * REC / (avg["h2d"] / 1e3) / 1e9, "d2h_GBps": n * REC / (avg["d2h"] / 1e3) / 1e9,
                        "timeline_ms": timeline,
-                       "pipeline": "double buffers: H2D of step s+1 and D2H of step s-1 on copy streams during sort s; "
-                                   "per-stream times are CUDA events around each copy and each bos_sort"}
+                       "pipeline": "double buffers on copy streams: H2D of step s+1 during sort s, after the D2H of "
+                                   "step s-1; per-stream times are CUDA events around each copy and each bos_sort"}
         del pin_in, pin_out, xin, xo
 
     # ---- comparators: plain one-level-per-launch form, GPU bitonic sort (rank-local) ----
