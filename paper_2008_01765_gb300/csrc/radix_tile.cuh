@@ -50,10 +50,11 @@ __device__ __forceinline__ void radix_tile(const typename RecT<R>::T* src, typen
       dr[it] = (uint32_t)(RecT<R>::key(rc[it]) >> shift) & 255u;
     }
   }
+  const bool full = t0 + kTile <= n;  // every item present: eight ballots decide a digit
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const uint32_t d = dr[it];
-    const uint32_t peers = ballot_peers(d, 9);  // 9 bits: 256 = no item
+    const uint32_t peers = full ? ballot_peers(d, 8) : ballot_peers(d, 9);  // 9 bits: 256 = no item
     const uint32_t lt = __popc(peers & lt_mask);
     const uint32_t r = wcnt[warp * 257 + d] + lt;
     __syncwarp();
