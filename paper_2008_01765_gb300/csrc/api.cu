@@ -341,19 +341,28 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
       // cheaper: up to 8-9 levels a pass with no cluster, the last pass stays the cluster kernel
       // (it needs its final buckets whole for the in-bin permutation). Costs in the same unit.
       const uint32_t kmin = orp_stream_min_k();
+      // An automatic plan keeps a batch to about 8 reals per output bucket on average (Z / 2^k in
+      // the first pass, Z / 2^(k+1) in a middle pass): more overrun the rings and the batch is
+      // redone in small rounds. A caller-given k is taken as given.
+      uint32_t lz = 0;
+      while ((1u << lz) < p->Z) ++lz;
+      const uint32_t kminf = p->k ? kmin : (lz >= 3 && lz - 3 > kmin ? lz - 3 : kmin);
+      const uint32_t kminm = p->k ? kmin : (lz >= 4 && lz - 4 > kmin ? lz - 4 : kmin);
       uint32_t ksf = (p->flags & BOS_FLAG_NO_STREAM) ? 0u : orp_stream_max_k(pl->R, p->Z, true, kMaxSmem);
       uint32_t ksm = ksf ? orp_stream_max_k(pl->R, p->Z, false, kMaxSmem) : 0u;
       if (p->k) {  // a caller-given k caps every pass (k = 1 is the plain form)
         ksf = p->k >= kmin && ksf ? (ksf < p->k ? ksf : p->k) : 0u;
         ksm = p->k >= kmin && ksm ? (ksm < p->k ? ksm : p->k) : 0u;
       }
+      if (ksf < kminf) ksf = 0;
+      if (ksm < kminm) ksm = 0;
       double sbest = 1e30;
       uint32_t sl = 0, snp = 0;
       for (uint32_t l = 1; ksf && l < L; ++l) {
         const uint32_t Cl = c_for(l, true), S = L - l;
         if (!Cl) continue;
         for (uint32_t np = 1; np + 1 <= kMaxPasses; ++np) {
-          if (S < np * kmin || (np > 1 && !ksm)) continue;
+          if (S < kminf + (np - 1) * kminm || (np > 1 && !ksm)) continue;
           if (S > ksf + (np - 1) * ksm) continue;
           const double c = kStreamFirst + (np - 1) * kStreamMid + kLast[ci(Cl)];
           if (c < sbest - 1e-9) {

@@ -26,8 +26,8 @@
 // its bucket's counter and records its slot index there; after a barrier a real whose bucket got
 // several reals in this batch counts how many of them have a smaller slot index (usually zero to
 // three), which is its stable rank. If a batch would add more reals to a ring than it has room
-// for (rare: a ring keeps at most kChunk-1 slots between batches), the batch is redone in rounds
-// of kSub slots.
+// for (rare: a ring keeps at most kChunk-1 slots between batches), the batch is redone in smaller
+// rounds: halved while a round would overflow, kSub slots at the least.
 //
 // Overflow (MergeSplit receives more than Z reals, Lemma 3.2): the level-(i+l) buckets of the
 // subproblem (l = 1..k-1) gather 2^l consecutive input buckets (2^(l-1) batches of the first pass)
@@ -91,9 +91,10 @@ __host__ __device__ inline StreamLayout stream_layout_n(int R, uint32_t Z, uint3
 }
 
 // The middle pass takes two input buckets per batch (four single-bucket stages) when Z fits one
-// item per thread per bucket and the stages fit; otherwise one bucket per batch, three stages.
+// item per thread per bucket, a batch's about Z reals average at most 8 per output bucket (more
+// would overrun the rings) and the stages fit; otherwise one bucket per batch, three stages.
 __host__ __device__ inline StreamLayout stream_layout(int R, uint32_t Z, uint32_t k, bool first) {
-  if (!first && Z <= (uint32_t)kST) {
+  if (!first && Z <= (uint32_t)kST && Z <= (8u << k)) {
     const StreamLayout p = stream_layout_n(R, Z, k, false, kStagesPaired, 1);
     if (p.total <= kSmemLimit) return p;
   }
@@ -316,11 +317,13 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
         }
       }
       __syncthreads();
-      if (check && flag[pb]) {  // a ring would overflow: undo the counts
+      if (check && flag[pb]) {  // a ring would overflow: undo the counts and clear the flag
 #pragma unroll
         for (uint32_t j = 0; j < kMaxItems; ++j)
           if (iu[j] < D) cntp[iu[j]] = 0u;
-        __syncthreads();
+        __syncthreads();  // every thread has seen the flag
+        if (tid == 0) flag[pb] = 0u;
+        __syncthreads();  // cleared before the next round can raise it
         return false;
       }
       if constexpr (FIRST) mbar_wait(smem_u32(bars + st), par, a.ctrl);
@@ -360,9 +363,19 @@ __global__ void __launch_bounds__(kST, 1) orp_stream_kernel(PassArgs a) {
     };
 
     if (!round(0, nslot, true)) {
-      for (uint32_t sb = 0; sb < nslot; sb += kSub) {
-        round(sb, min(sb + kSub, nslot), false);
-        __syncthreads();  // the next round reuses this round's counters
+      // a ring would overflow: redo the batch in smaller rounds, halving after every round that
+      // would overflow (kSub slots at the least, which no ring can overflow) and doubling after
+      // every round that fits
+      uint32_t sz = nslot / 2 > kSub ? nslot / 2 : kSub;
+      for (uint32_t sb = 0; sb < nslot;) {
+        const uint32_t hi = sb + sz < nslot ? sb + sz : nslot;
+        if (round(sb, hi, sz > kSub)) {
+          sb = hi;
+          sz = 2 * sz < nslot ? 2 * sz : nslot;
+          __syncthreads();  // the next round reuses this round's counters
+        } else {
+          sz = sz / 2 > kSub ? sz / 2 : kSub;
+        }
       }
     }
     // ---- after the batch: its stage is free; level blocks that end here are checked ----

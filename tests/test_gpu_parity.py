@@ -421,7 +421,8 @@ STREAM_CASES = [
     # (n, Z, rec_bytes, k): automatic plans whose first and middle passes run the streaming kernel
     # (orp_stream.cu). Ragged n (groups of unequal size), the Z values it takes, both widths.
     ((1 << 20) + 3, 512, 16, 0), (1 << 20, 256, 8, 0), (300001, 96, 8, 0), (4097, 64, 8, 0),
-    (1 << 21, 2048, 16, 0), ((1 << 22) + 12345, 1024, 16, 0), (1 << 24, 512, 16, 0), (1 << 21, 64, 8, 0),
+    (1 << 21, 2048, 8, 0), ((1 << 22) + 12345, 1024, 16, 0), (1 << 24, 512, 16, 0), (1 << 21, 64, 8, 0),
+    (1 << 25, 1024, 16, 0),
     # k = 5 with Z = 2048: a batch brings 32-64 reals to each of the 32 output buckets, more than a
     # ring holds, so every batch is redone in rounds of 16 slots (the kernel's slow path)
     (1 << 20, 2048, 8, 5), ((1 << 20) + 1, 2048, 16, 5), (1 << 20, 1024, 16, 6),
