@@ -143,7 +143,7 @@ struct Plan {
   // workspace offsets
   size_t off_ctrl = 0, off_rec[2] = {0, 0}, off_tag[2] = {0, 0}, off_status = 0;
   size_t off_tmp = 0, off_hist = 0, off_dbase = 0, off_rstatus = 0, off_ord = 0, off_load = 0, total = 0;
-  size_t off_joint = 0, off_gstart = 0, off_rlist = 0, off_first = 0, off_meta = 0, off_spill = 0;
+  size_t off_joint = 0, off_gstart = 0, off_rlist = 0, off_first = 0, off_meta = 0, off_spill = 0, off_ridx = 0;
   uint64_t orp_tiles = 0, radix_tiles = 0;
 };
 
@@ -427,7 +427,8 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
     pl->off_gstart = off;  off = align256(off + 65537 * 8);
     pl->off_rlist = off;   off = align256(off + 65537 * 4);
     pl->off_first = off;   off = align256(off + 257 * 8);
-    pl->off_meta = off;    off = align256(off + 16);
+    pl->off_meta = off;    off = align256(off + 32);
+    pl->off_ridx = off;    off = align256(off + 2 * 65537 * 4);
     pl->off_spill = off;   off = align256(off + hybrid_spill_bytes(n, pl->R));
   }
   pl->total = off;
@@ -589,6 +590,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
     ha.rlist = (uint32_t*)(ws + pl.off_rlist);
     ha.first = (unsigned long long*)(ws + pl.off_first);
     ha.meta = (uint32_t*)(ws + pl.off_meta);
+    ha.ridx = (uint32_t*)(ws + pl.off_ridx);
     ha.status = ra.status;
     ha.scratch = (unsigned char*)(ws + pl.off_spill);
     ha.local_ctas = hybrid_local_ctas(n, pl.R);

@@ -145,7 +145,9 @@ struct HybridArgs {
   unsigned long long* gstart;       // [65537] group starts
   uint32_t* rlist;                  // [65537] first group of every range
   unsigned long long* first;        // [257] partition tiles before every top-digit bucket
-  uint32_t* meta;                   // [4] mode, top varying digit, next varying digit, ranges
+  uint32_t* meta;                   // [8] mode, top varying digit, next varying digit, ranges,
+                                    // large ranges, small ranges
+  uint32_t* ridx;                   // [2][65537] the large ranges, then (at 65537) the small ones
   unsigned long long* status;       // look-back words for radix_tiles(n) + 256 tiles
   unsigned char* scratch;           // hybrid_spill_bytes(n, R): one spill buffer per on-chip-sort CTA
   uint32_t local_ctas;              // = hybrid_local_ctas(n, R)

@@ -34,6 +34,12 @@ constexpr uint32_t kLocalMaxCtas = 192;  // spill buffers in the workspace (one 
 constexpr uint32_t kTagMsd1 = 12, kTagMsd2 = 13;
 constexpr uint32_t kTicketMsd1 = 10, kTicketMsd2 = 11, kTicketLocal = 12;
 constexpr uint32_t kWarpMax = 256;        // largest sub-bucket one warp sorts in registers
+constexpr int kSThreads = 256;            // warp-per-range kernel
+constexpr int kSEPL = 16;                 // its words per lane
+constexpr uint32_t kSmallMax = 32 * kSEPL;  // ranges of at most this many records: one warp each
+constexpr uint32_t kRangeList = 65537;    // the small ranges' list starts here in ridx
+constexpr uint32_t kTicketSmall = 13;
+static_assert(kGroups <= 64u * kPlanThreads, "the plan keeps one bit per range in a 64-bit word");
 
 template <int R> struct Local;
 template <> struct Local<16> { static constexpr uint32_t kCap = 19456; };  // 10 B per record on chip
@@ -228,6 +234,30 @@ __global__ void __launch_bounds__(kPlanThreads) sort_plan_kernel(HybridArgs a) {
     a.rlist[nranges] = G;
     a.meta[3] = (uint32_t)nranges;
   }
+  __syncthreads();  // the range list and the group starts are written
+  {  // ranges of at most kSmallMax records go to the warp kernel, larger ones to the CTA kernel
+    const uint32_t NR = (uint32_t)nranges, rper = (NR + kPlanThreads - 1) / kPlanThreads;
+    const uint32_t r0 = tid * rper < NR ? tid * rper : NR, r1 = r0 + rper < NR ? r0 + rper : NR;
+    // at most 64 ranges per thread (at most 65536 ranges): one bit each, set for a small range
+    unsigned long long small = 0;
+#pragma unroll 8
+    for (uint32_t r = r0; r < r1; ++r)
+      if (a.gstart[a.rlist[r + 1]] - a.gstart[a.rlist[r]] <= kSmallMax) small |= 1ull << (r - r0);
+    unsigned long long tsm = 0, tbg = 0;
+    const unsigned long long nsm = (unsigned long long)__popcll(small);
+    unsigned long long xs = plan_scan(nsm, s_w, &tsm);
+    unsigned long long xb = plan_scan((r1 - r0) - nsm, s_w, &tbg);
+    for (uint32_t r = r0; r < r1; ++r) {
+      if ((small >> (r - r0)) & 1ull)
+        a.ridx[kRangeList + xs++] = r;
+      else
+        a.ridx[xb++] = r;
+    }
+    if (tid == 0) {
+      a.meta[4] = (uint32_t)tbg;
+      a.meta[5] = (uint32_t)tsm;
+    }
+  }
   if (mode == 3) {  // MSD2 tiles: every dA bucket is cut into tiles of its own
     const uint64_t tb = tid < 256 ? ((uint64_t)a.hist[dA * 256 + tid] + kTile - 1) / kTile : 0ull;
     unsigned long long ttot = 0;
@@ -420,15 +450,16 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
   Rec* dst = sort_buf<R>(a, mode, mode);
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t lt_mask = lanemask_lt();
-  const uint32_t nranges = a.meta[3];
+  const uint32_t nbig = a.meta[4];  // this kernel's ranges: those of more than kSmallMax records
   // the digit read 1 counts: the top varying digit of a one-group range under this mode
   const uint32_t dspec = mode == 3 ? D - 3 : mode == 2 ? D - 2 : D - 1;
 
   while (true) {
     if (tid == 0) misc[0] = atomicAdd(&a.ctrl->tickets[kTicketLocal], 1u);
     __syncthreads();
-    const uint32_t r = misc[0];
-    if (r >= nranges) break;
+    const uint32_t ti = misc[0];
+    if (ti >= nbig) break;
+    const uint32_t r = a.ridx[ti];
     const uint64_t lo = a.gstart[a.rlist[r]];
     const uint64_t m64 = a.gstart[a.rlist[r + 1]] - lo;
     if (m64 == 0 || m64 > kCap) {  // empty; or more than the plan allows (never: the counts bound it)
@@ -658,6 +689,108 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
   }
 }
 
+// Ascending bitonic sort of (key, position) pairs in registers, the same network as warp_sort:
+// lane l holds elements l * EPL .. l * EPL + EPL - 1. Positions are distinct; padding is the
+// largest pair.
+template <typename Key, int EPL>
+__device__ __forceinline__ void warp_sort_pairs(Key (&k)[EPL], uint32_t (&x)[EPL], uint32_t lane) {
+  auto less = [](Key ka, uint32_t xa, Key kb, uint32_t xb) { return ka < kb || (ka == kb && xa < xb); };
+#pragma unroll
+  for (int kk = 2; kk <= 32 * EPL; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j < EPL) {
+#pragma unroll
+        for (int r = 0; r < EPL; ++r) {
+          if ((r & j) == 0) {
+            const bool up = ((lane * EPL + (uint32_t)r) & (uint32_t)kk) == 0;
+            const bool sw = less(k[r | j], x[r | j], k[r], x[r]) == up;
+            const Key tk = k[r];
+            const uint32_t tx = x[r];
+            k[r] = sw ? k[r | j] : k[r];
+            x[r] = sw ? x[r | j] : x[r];
+            k[r | j] = sw ? tk : k[r | j];
+            x[r | j] = sw ? tx : x[r | j];
+          }
+        }
+      } else {
+        const uint32_t lj = (uint32_t)j / EPL;
+#pragma unroll
+        for (int r = 0; r < EPL; ++r) {
+          const Key ok = __shfl_xor_sync(0xFFFFFFFFu, k[r], lj);
+          const uint32_t ox = __shfl_xor_sync(0xFFFFFFFFu, x[r], lj);
+          const bool up = ((lane * EPL + (uint32_t)r) & (uint32_t)kk) == 0;
+          const bool keep_min = ((lane & lj) == 0) == up;
+          if (less(ok, ox, k[r], x[r]) == keep_min) {
+            k[r] = ok;
+            x[r] = ox;
+          }
+        }
+      }
+    }
+  }
+}
+
+// One range of m <= 32 * EPL records sorted by one warp: keys and positions into registers (in
+// any arrangement: the network sorts them all), sorted, the order through shared memory, then the
+// records gathered into place with coalesced writes.
+template <int R, int EPL>
+__device__ __forceinline__ void small_range(const typename RecT<R>::T* in, typename RecT<R>::T* out, uint32_t m,
+                                            uint16_t* sidx, uint32_t lane) {
+  using Key = typename RecT<R>::Key;
+  Key k[EPL];
+  uint32_t x[EPL];
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    const uint32_t e = (uint32_t)r * 32 + lane;
+    k[r] = e < m ? load_key<R>(in + e) : ~Key(0);
+    x[r] = e < m ? e : 0xFFFFFFFFu;
+  }
+  warp_sort_pairs<Key, EPL>(k, x, lane);
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    const uint32_t e = lane * EPL + (uint32_t)r;
+    if (e < m) sidx[e] = (uint16_t)x[r];
+  }
+  __syncwarp();
+  for (uint32_t e = lane; e < m; e += 32) out[e] = in[sidx[e]];
+  __syncwarp();
+}
+
+// The ranges of at most kSmallMax records (many small groups: n between about 2^22 and 2^27 for
+// 16-byte records), a warp each, taken by ticket; no block-wide barrier.
+template <int R>
+__global__ void __launch_bounds__(kSThreads) local_small_kernel(HybridArgs a) {
+  using Rec = typename RecT<R>::T;
+  const uint32_t mode = a.ctrl->sort_mode;
+  if (mode == 0) return;
+  __shared__ uint16_t sidx[kSThreads / 32][kSmallMax];
+  const Rec* src = sort_buf<R>(a, mode, mode - 1);
+  Rec* dst = sort_buf<R>(a, mode, mode);
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint32_t nsmall = a.meta[5];
+  while (true) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&a.ctrl->tickets[kTicketSmall], 1u);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= nsmall) break;
+    const uint32_t r = a.ridx[kRangeList + t];
+    const uint64_t lo = a.gstart[a.rlist[r]];
+    const uint64_t m64 = a.gstart[a.rlist[r + 1]] - lo;
+    if (m64 == 0) continue;
+    if (m64 > kSmallMax) {  // never: the plan lists only small ranges here
+      if (lane == 0) atomicExch(&a.ctrl->bad, 1u);
+      continue;
+    }
+    const uint32_t m = (uint32_t)m64;
+    if (m <= 32) small_range<R, 1>(src + lo, dst + lo, m, sidx[w], lane);
+    else if (m <= 64) small_range<R, 2>(src + lo, dst + lo, m, sidx[w], lane);
+    else if (m <= 128) small_range<R, 4>(src + lo, dst + lo, m, sidx[w], lane);
+    else if (m <= 256) small_range<R, 8>(src + lo, dst + lo, m, sidx[w], lane);
+    else small_range<R, 16>(src + lo, dst + lo, m, sidx[w], lane);
+  }
+}
+
 int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -700,6 +833,8 @@ cudaError_t launch_r(const HybridArgs& a, int stage, cudaStream_t st) {
       break;
     }
     default: {
+      local_small_kernel<R><<<(unsigned)sms * 8, kSThreads, 0, st>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
       const uint32_t smem = local_smem_bytes<R>();
       if ((e = cudaFuncSetAttribute(local_sort_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
           cudaSuccess)
