@@ -35,10 +35,9 @@ constexpr uint32_t kTagMsd1 = 12, kTagMsd2 = 13;
 constexpr uint32_t kTicketMsd1 = 10, kTicketMsd2 = 11, kTicketLocal = 12;
 constexpr uint32_t kWarpMax = 256;        // largest sub-bucket one warp sorts in registers
 constexpr int kSThreads = 256;            // warp-per-range kernel
-constexpr int kSEPL = 16;                 // its words per lane
-constexpr uint32_t kSmallMax = 32 * kSEPL;  // ranges of at most this many records: one warp each
+constexpr uint32_t kSmallMax = 1024;      // ranges of at most this many records: one warp each
 constexpr uint32_t kRangeList = 65537;    // the small ranges' list starts here in ridx
-constexpr uint32_t kTicketSmall = 13;
+constexpr uint32_t kTicketSmall = 13;     // and 14
 static_assert(kGroups <= 64u * kPlanThreads, "the plan keeps one bit per range in a 64-bit word");
 
 template <int R> struct Local;
@@ -691,42 +690,60 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
 
 // Ascending bitonic sort of (key, position) pairs in registers, the same network as warp_sort:
 // lane l holds elements l * EPL .. l * EPL + EPL - 1. Positions are distinct; padding is the
-// largest pair.
+// largest pair. The stage loops stay rolled (one body per partner distance below EPL and one for
+// the distances across lanes), so the code of every size fits the instruction cache.
+template <typename Key>
+__device__ __forceinline__ bool pair_less(Key ka, uint32_t xa, Key kb, uint32_t xb) {
+  return ka < kb || (ka == kb && xa < xb);
+}
+
+template <typename Key, int EPL, int J>
+__device__ __forceinline__ void pair_stage_lane(Key (&k)[EPL], uint32_t (&x)[EPL], uint32_t lane, uint32_t kk) {
+  if constexpr (J < EPL) {
+#pragma unroll
+    for (int r = 0; r < EPL; ++r) {
+      if ((r & J) == 0) {
+        const bool up = ((lane * EPL + (uint32_t)r) & kk) == 0;
+        const bool sw = pair_less(k[r | J], x[r | J], k[r], x[r]) == up;
+        const Key tk = k[r];
+        const uint32_t tx = x[r];
+        k[r] = sw ? k[r | J] : k[r];
+        x[r] = sw ? x[r | J] : x[r];
+        k[r | J] = sw ? tk : k[r | J];
+        x[r | J] = sw ? tx : x[r | J];
+      }
+    }
+  }
+}
+
+template <typename Key, int EPL>
+__device__ __forceinline__ void pair_stage_cross(Key (&k)[EPL], uint32_t (&x)[EPL], uint32_t lane, uint32_t kk,
+                                                 uint32_t lj) {
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    const Key ok = __shfl_xor_sync(0xFFFFFFFFu, k[r], lj);
+    const uint32_t ox = __shfl_xor_sync(0xFFFFFFFFu, x[r], lj);
+    const bool up = ((lane * EPL + (uint32_t)r) & kk) == 0;
+    const bool keep_min = ((lane & lj) == 0) == up;
+    if (pair_less(ok, ox, k[r], x[r]) == keep_min) {
+      k[r] = ok;
+      x[r] = ox;
+    }
+  }
+}
+
 template <typename Key, int EPL>
 __device__ __forceinline__ void warp_sort_pairs(Key (&k)[EPL], uint32_t (&x)[EPL], uint32_t lane) {
-  auto less = [](Key ka, uint32_t xa, Key kb, uint32_t xb) { return ka < kb || (ka == kb && xa < xb); };
-#pragma unroll
-  for (int kk = 2; kk <= 32 * EPL; kk <<= 1) {
-#pragma unroll
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      if (j < EPL) {
-#pragma unroll
-        for (int r = 0; r < EPL; ++r) {
-          if ((r & j) == 0) {
-            const bool up = ((lane * EPL + (uint32_t)r) & (uint32_t)kk) == 0;
-            const bool sw = less(k[r | j], x[r | j], k[r], x[r]) == up;
-            const Key tk = k[r];
-            const uint32_t tx = x[r];
-            k[r] = sw ? k[r | j] : k[r];
-            x[r] = sw ? x[r | j] : x[r];
-            k[r | j] = sw ? tk : k[r | j];
-            x[r | j] = sw ? tx : x[r | j];
-          }
-        }
-      } else {
-        const uint32_t lj = (uint32_t)j / EPL;
-#pragma unroll
-        for (int r = 0; r < EPL; ++r) {
-          const Key ok = __shfl_xor_sync(0xFFFFFFFFu, k[r], lj);
-          const uint32_t ox = __shfl_xor_sync(0xFFFFFFFFu, x[r], lj);
-          const bool up = ((lane * EPL + (uint32_t)r) & (uint32_t)kk) == 0;
-          const bool keep_min = ((lane & lj) == 0) == up;
-          if (less(ok, ox, k[r], x[r]) == keep_min) {
-            k[r] = ok;
-            x[r] = ox;
-          }
-        }
-      }
+#pragma unroll 1
+  for (uint32_t kk = 2; kk <= 32u * EPL; kk <<= 1) {
+#pragma unroll 1
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= (uint32_t)EPL) pair_stage_cross<Key, EPL>(k, x, lane, kk, j / EPL);
+      else if (j == 1) pair_stage_lane<Key, EPL, 1>(k, x, lane, kk);
+      else if (j == 2) pair_stage_lane<Key, EPL, 2>(k, x, lane, kk);
+      else if (j == 4) pair_stage_lane<Key, EPL, 4>(k, x, lane, kk);
+      else if (j == 8) pair_stage_lane<Key, EPL, 8>(k, x, lane, kk);
+      else pair_stage_lane<Key, EPL, 16>(k, x, lane, kk);
     }
   }
 }
@@ -757,37 +774,44 @@ __device__ __forceinline__ void small_range(const typename RecT<R>::T* in, typen
   __syncwarp();
 }
 
-// The ranges of at most kSmallMax records (many small groups: n between about 2^22 and 2^27 for
-// 16-byte records), a warp each, taken by ticket; no block-wide barrier.
-template <int R>
+// The ranges of at most kSmallMax records (many small groups: n between about 2^22 and 2^28 for
+// 16-byte records), a warp each, taken by ticket; no block-wide barrier. Two launches share the
+// list: BIG = false sorts the ranges of at most 512 records (16 pairs per lane at most, so more
+// warps fit an SM), BIG = true those of 513 to 1024 (32 pairs per lane).
+template <int R, bool BIG>
 __global__ void __launch_bounds__(kSThreads) local_small_kernel(HybridArgs a) {
   using Rec = typename RecT<R>::T;
+  constexpr uint32_t kMax = BIG ? 1024u : 512u;
   const uint32_t mode = a.ctrl->sort_mode;
   if (mode == 0) return;
-  __shared__ uint16_t sidx[kSThreads / 32][kSmallMax];
+  __shared__ uint16_t sidx[kSThreads / 32][kMax];
   const Rec* src = sort_buf<R>(a, mode, mode - 1);
   Rec* dst = sort_buf<R>(a, mode, mode);
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
   const uint32_t nsmall = a.meta[5];
   while (true) {
     uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(&a.ctrl->tickets[kTicketSmall], 1u);
+    if (lane == 0) t = atomicAdd(&a.ctrl->tickets[BIG ? kTicketSmall + 1 : kTicketSmall], 1u);
     t = __shfl_sync(0xFFFFFFFFu, t, 0);
     if (t >= nsmall) break;
     const uint32_t r = a.ridx[kRangeList + t];
     const uint64_t lo = a.gstart[a.rlist[r]];
     const uint64_t m64 = a.gstart[a.rlist[r + 1]] - lo;
-    if (m64 == 0) continue;
     if (m64 > kSmallMax) {  // never: the plan lists only small ranges here
       if (lane == 0) atomicExch(&a.ctrl->bad, 1u);
       continue;
     }
     const uint32_t m = (uint32_t)m64;
-    if (m <= 32) small_range<R, 1>(src + lo, dst + lo, m, sidx[w], lane);
-    else if (m <= 64) small_range<R, 2>(src + lo, dst + lo, m, sidx[w], lane);
-    else if (m <= 128) small_range<R, 4>(src + lo, dst + lo, m, sidx[w], lane);
-    else if (m <= 256) small_range<R, 8>(src + lo, dst + lo, m, sidx[w], lane);
-    else small_range<R, 16>(src + lo, dst + lo, m, sidx[w], lane);
+    if (m == 0 || (m > 512) != BIG) continue;  // the other launch's range
+    if constexpr (BIG) {
+      small_range<R, 32>(src + lo, dst + lo, m, sidx[w], lane);
+    } else {
+      if (m <= 32) small_range<R, 1>(src + lo, dst + lo, m, sidx[w], lane);
+      else if (m <= 64) small_range<R, 2>(src + lo, dst + lo, m, sidx[w], lane);
+      else if (m <= 128) small_range<R, 4>(src + lo, dst + lo, m, sidx[w], lane);
+      else if (m <= 256) small_range<R, 8>(src + lo, dst + lo, m, sidx[w], lane);
+      else small_range<R, 16>(src + lo, dst + lo, m, sidx[w], lane);
+    }
   }
 }
 
@@ -833,7 +857,9 @@ cudaError_t launch_r(const HybridArgs& a, int stage, cudaStream_t st) {
       break;
     }
     default: {
-      local_small_kernel<R><<<(unsigned)sms * 8, kSThreads, 0, st>>>(a);
+      local_small_kernel<R, false><<<(unsigned)sms * 8, kSThreads, 0, st>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      local_small_kernel<R, true><<<(unsigned)sms * 4, kSThreads, 0, st>>>(a);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       const uint32_t smem = local_smem_bytes<R>();
       if ((e = cudaFuncSetAttribute(local_sort_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=

@@ -683,9 +683,10 @@ HYBRID_CASES = [
     (1 << 20, 16, "sorted", 2), (1 << 20, 16, "reverse", 0), (200003, 16, "equal", 0),
     (1 << 20, 16, "low16_zero", 2), (1 << 20, 16, "top_two_values", 0), (1 << 20, 8, "half_equal", 0),
     (1 << 20, 16, "few_values", None), (1 << 22, 16, "d6_few", 2), (1 << 24, 8, "uniform", 3),
-    # ranges of at most 512 records go to the warp-per-range kernel: one whole array, or many
-    # single-group ranges of about 256 / 512 records
+    # ranges of at most 1024 records go to the warp-per-range kernels: one whole array, or many
+    # single-group ranges of about 256 / 512 / 1024 records
     (500, 16, "uniform", 1), (512, 8, "dup1024", 1), (1 << 24, 16, "uniform", 3), (1 << 25, 16, "uniform", 3),
+    (1000, 16, "uniform", 1), (1 << 26, 16, "uniform", 3),
 ]
 
 
