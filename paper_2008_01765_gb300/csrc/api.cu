@@ -86,6 +86,9 @@ int prof_begin(cudaStream_t st, int cls, double bytes, uint32_t digit = 0) {
 void prof_end(int i, cudaStream_t st) {
   if (i >= 0) cudaEventRecord(g_prof.ev[2 * i + 1], st);
 }
+// Launches that run inside another launch's profile event still count as launches.
+void count_launches(uint64_t k) { g_prof.total_launches.fetch_add(k, std::memory_order_relaxed); }
+
 cudaError_t zero_async(void* p, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return cudaSuccess;
   const size_t words = bytes / 16 + 1;
@@ -613,7 +616,10 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
       prof_end(ev, st);
       ev = prof_begin(st, kKPrep, 0.0);
       BOS_CUDA(launch_radix_prep(ra, pl.R, st));
-      if (hybrid) BOS_CUDA(launch_hybrid(ha, pl.R, 1, st));
+      if (hybrid) {
+        BOS_CUDA(launch_hybrid(ha, pl.R, 1, st));
+        count_launches(1);  // the plan kernel, inside the prep event
+      }
       prof_end(ev, st);
     }
     if (oblivious) {
@@ -685,6 +691,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         const double tb = (double)pl.B * pl.Z * (2.0 + (first ? 0.0 : 4.0));  // rows out, tags in
         const int evt = prof_begin(st, kKPerm, tb);
         BOS_CUDA(launch_perm_table(ta, st, trace));
+        count_launches(1);  // final loads and table: two kernels in one event
         prof_end(evt, st);
       }
       const int ev = prof_begin(st, cls, in_b + out_b);
@@ -704,6 +711,7 @@ bos_status run(const void* d_in, void* d_out, uint64_t n, const bos_params* p, v
         for (int stage = 2; stage <= 4; ++stage) {
           const int ev = prof_begin(st, stage == 4 ? kKLocal : kKMsd, 2.0 * n * pl.R, (uint32_t)stage);
           BOS_CUDA(launch_hybrid(ha, pl.R, stage, st));
+          if (stage == 4) count_launches(2);  // two warp-per-range launches and the CTA one
           prof_end(ev, st);
         }
       for (uint32_t d = 0; d < pl.digits; ++d) {  // skipped when the hybrid sort runs
