@@ -404,17 +404,15 @@ __device__ __forceinline__ uint32_t row_peers(uint32_t dg, bool full) {
   return full ? ballot_peers(dg, 8) : ballot_peers(dg, 9);
 }
 
-// Per-warp counts of digit d of the keys at positions [wlo, whi) (rows of 32).
+// Per-warp counts of digit d of the keys at positions [wlo, whi) (shared-memory atomics on the warp's
+// own counters: counts need no ranks).
 template <int R>
 __device__ __forceinline__ void local_count(const typename RecT<R>::T* in, uint32_t* wc, uint32_t d, uint32_t wlo,
                                             uint32_t whi, uint32_t lane, uint32_t warp, uint32_t lt_mask) {
   for (uint32_t b = wlo; b < whi; b += 32) {
     const uint32_t j = b + lane;
     const bool valid = j < whi;
-    const uint32_t dg = valid ? (uint32_t)((load_key<R>(in + j) >> (8 * d)) & 255u) : 256u;
-    const uint32_t peers = row_peers(dg, b + 32 <= whi);
-    if (valid && (peers & lt_mask) == 0) wc[warp * 257 + dg] += __popc(peers);
-    __syncwarp();
+    if (valid) atomicAdd(&wc[warp * 257 + (uint32_t)((load_key<R>(in + j) >> (8 * d)) & 255u)], 1u);
   }
 }
 
@@ -495,10 +493,8 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
           kand &= kk[u];
           kor |= kk[u];
         }
-        const uint32_t dg = valid ? (uint32_t)((kk[u] >> (8 * dspec)) & 255u) : 256u;
-        const uint32_t peers = row_peers(dg, b0 + u * 32 + 32 <= whi);
-        if (valid && (peers & lt_mask) == 0) wc[warp * 257 + dg] += __popc(peers);
-        __syncwarp();
+        // counts only (no ranks): one shared-memory atomic per key on the warp's own counters
+        if (valid) atomicAdd(&wc[warp * 257 + (uint32_t)((kk[u] >> (8 * dspec)) & 255u)], 1u);
       }
     }
 #pragma unroll
