@@ -270,7 +270,11 @@ bos_status make_plan(uint64_t n, const bos_params* p, bool sort, Plan* pl, uint3
     static const double kMid[5] = {1.0, 1.371, 1.623, 1.919, 2.49};  // C = 1, 2, 4, 8, 16
     static const double kFirst[5] = {1.269, 1.496, 1.667, 2.168, 2.63};
     static const double kLast[5] = {1.219, 1.459, 1.723, 2.212, 2.63};
-    static const double kStreamFirst = 0.85, kStreamMid = 1.15;  // streaming kernel, k up to 8-9
+    // Streaming kernel, k up to 8-9: set so that a streaming plan wins where it saves a pass. Its
+    // measured ratios at n = 2^30, Z = 1024 are 1.76 (first, k = 8) and 1.92 (paired middle), and
+    // with those the streaming plan still wins there; at small Z they would pick cluster plans
+    // that were never measured against it.
+    static const double kStreamFirst = 0.85, kStreamMid = 1.15;
     const uint32_t kcap = p->k ? p->k : kMaxKFast;
     auto c_for = [&](uint32_t k, bool last) -> uint32_t {  // smallest C holding k levels; 0: none
       if (k > kcap) return 0;
