@@ -408,7 +408,7 @@ __device__ __forceinline__ uint32_t row_peers(uint32_t dg, bool full) {
 // own counters: counts need no ranks).
 template <int R>
 __device__ __forceinline__ void local_count(const typename RecT<R>::T* in, uint32_t* wc, uint32_t d, uint32_t wlo,
-                                            uint32_t whi, uint32_t lane, uint32_t warp, uint32_t lt_mask) {
+                                            uint32_t whi, uint32_t lane, uint32_t warp) {
   for (uint32_t b = wlo; b < whi; b += 32) {
     const uint32_t j = b + lane;
     const bool valid = j < whi;
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
       if (dC != counted) {
         for (uint32_t x = tid; x < kLWarps * 257; x += kLThreads) wc[x] = 0;
         __syncthreads();
-        local_count<R>(in, wc, dC, wlo, whi, lane, warp, lt_mask);
+        local_count<R>(in, wc, dC, wlo, whi, lane, warp);
         __syncthreads();
         counted = dC;
       }
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kLThreads, 1) local_sort_kernel(HybridArgs a) 
     if (d != counted) {
       for (uint32_t x = tid; x < kLWarps * 257; x += kLThreads) wc[x] = 0;
       __syncthreads();
-      local_count<R>(in, wc, d, wlo, whi, lane, warp, lt_mask);
+      local_count<R>(in, wc, d, wlo, whi, lane, warp);
     }
     __syncthreads();
     uint32_t q = 0;
