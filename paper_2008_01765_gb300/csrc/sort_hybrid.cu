@@ -12,8 +12,10 @@
 //   3. modes 2, 3: a stable partition of the whole array by dA (the onesweep tile of the LSD pass);
 //   4. mode 3: a stable partition by dB inside every dA bucket (tiles per bucket, the look-back
 //      stopping at the bucket's first tile);
-//   5. every range is sorted on chip, stably, by the digits that vary inside it (LSD order), and
-//      its records are then gathered into place.
+//   5. every range is sorted on chip by (key, position) and its records gathered into place: a
+//      range of at most 1024 records by one warp in registers, a larger one by a CTA (a stable
+//      partition by the range's top varying digit in shared memory, then a warp sort of every
+//      sub-bucket; LSD passes over the varying digits when that does not fit).
 // The partitions are stable and a range holds whole groups in key order, so sorting every range
 // by key sorts the array; ties keep the ORP's order. HBM passes: the mode's count (1 to 3) plus
 // the histogram, against 1 + the live digits for the LSD sort.
